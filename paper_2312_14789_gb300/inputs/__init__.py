@@ -1,0 +1,328 @@
+"""Seeded synthetic workloads for the meshless LBM step.
+
+Only geometry lives here: node positions, node classes, solid disks, the box
+and its side types, prescribed boundary values (density and velocity for
+equilibrium-overwrite nodes), node areas and plain random arrays.  No lattice
+Boltzmann arithmetic (equilibria, weights, interpolation, collision) is
+performed here, so both the CUDA path and the FP64 oracle can read the same
+inputs without sharing any part of the method.
+
+Workload shapes follow the paper's test cases:
+  * periodic Poiseuille channel on a jittered grid (plain MLBM, Sec. 2.2);
+  * cylinder in a channel with a refined scattered node set (Sec. 3.1);
+  * porous box of random non-overlapping disks, periodic in x with walls at
+    the top and bottom and wall nodes placed on the solid surfaces (Sec. 3.2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# node classes (also the values the C-ABI and the oracle accept)
+FLUID, WALL, EQ = 0, 1, 2
+# side types
+PERIODIC, SOLID, OPEN = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def build_sampler(force: bool = False) -> str:
+    """Compile the Poisson-disk sampler (plain C) in-tree; return the .so path."""
+    out_dir = os.path.join(_HERE, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    so = os.path.join(out_dir, "libpoisson.so")
+    src = os.path.join(_HERE, "poisson.c")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        tmp = so + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, src, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            lib = ctypes.CDLL(build_sampler())
+            lib.pd_sample.restype = ctypes.c_int64
+            lib.pd_sample.argtypes = [
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int, ctypes.c_int,
+                ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                ctypes.c_void_p, ctypes.c_int64,
+                ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]
+            _LIB = lib
+    return _LIB
+
+
+@dataclass
+class Workload:
+    """A node set plus everything the boundary treatment needs to know."""
+    name: str
+    xy: np.ndarray                 # (n, 2) float64 node positions
+    node_class: np.ndarray         # (n,) uint8: FLUID / WALL / EQ
+    box: tuple                     # (x0, y0, x1, y1)
+    sides: tuple                   # (left, right, bottom, top): PERIODIC / SOLID / OPEN
+    disks: np.ndarray              # (m, 3) float64: cx, cy, r (solid)
+    eq_values: np.ndarray          # (n, 3) float64: rho, ux, uy for EQ nodes, zero elsewhere
+    area: np.ndarray               # (n,) float64 node areas (same length unit as xy)
+    h_ref: float = 1.0             # reference node spacing
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.xy.shape[0])
+
+    def fluid_area(self) -> float:
+        x0, y0, x1, y1 = self.box
+        return float((x1 - x0) * (y1 - y0) - np.sum(np.pi * self.disks[:, 2] ** 2)) if len(self.disks) \
+            else float((x1 - x0) * (y1 - y0))
+
+
+def _sample(box, periodic, rgrid, disks, clear_frac, fixed, seed, max_out, k_tries=30):
+    x0, y0, x1, y1 = box
+    rgrid = np.ascontiguousarray(rgrid, dtype=np.float64)
+    disks = np.ascontiguousarray(disks, dtype=np.float64).reshape(-1, 3)
+    fixed = np.ascontiguousarray(fixed, dtype=np.float64).reshape(-1, 2)
+    out = np.empty((max_out, 2), dtype=np.float64)
+    n = _lib().pd_sample(x0, y0, x1, y1, int(periodic[0]), int(periodic[1]),
+                         rgrid.ctypes.data, rgrid.shape[1], rgrid.shape[0],
+                         disks.ctypes.data if len(disks) else None, len(disks), float(clear_frac),
+                         fixed.ctypes.data if len(fixed) else None, len(fixed),
+                         np.uint64(seed), k_tries, out.ctypes.data, max_out)
+    if n < 0:
+        raise RuntimeError("Poisson-disk sampler ran out of room; raise max_out")
+    return out[:n].copy()
+
+
+# --------------------------------------------------------------------------
+# Plain grids
+# --------------------------------------------------------------------------
+def lattice(nx: int, ny: int, h: float = 1.0, walls_y: bool = False, name: str = "lattice") -> Workload:
+    """Regular square lattice.  Doubly periodic, or periodic in x with wall
+    nodes on rows y=0 and y=(ny-1)h when walls_y is set."""
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    xy = np.stack([ix.ravel() * h, iy.ravel() * h], axis=1).astype(np.float64)
+    cls = np.zeros(len(xy), np.uint8)
+    if walls_y:
+        box = (0.0, 0.0, nx * h, (ny - 1) * h)
+        sides = (PERIODIC, PERIODIC, SOLID, SOLID)
+        cls[(iy.ravel() == 0) | (iy.ravel() == ny - 1)] = WALL
+        area = np.full(len(xy), h * h)
+        area[cls == WALL] = 0.5 * h * h
+    else:
+        box = (0.0, 0.0, nx * h, ny * h)
+        sides = (PERIODIC, PERIODIC, PERIODIC, PERIODIC)
+        area = np.full(len(xy), h * h)
+    return Workload(name, xy, cls, box, sides, np.zeros((0, 3)), np.zeros((len(xy), 3)), area, h,
+                    {"nx": nx, "ny": ny})
+
+
+def lattice_channel(nx: int, ny: int, y_offset: float = 0.5, h: float = 1.0) -> Workload:
+    """Regular lattice, periodic in x, rows at y = (j + y_offset) h for
+    j = 0..ny-1, solid walls at y = 0 and y = (ny - 1 + 2 y_offset) h, so both
+    walls sit y_offset*h from the outer rows (0.5: half-way between nodes;
+    0: wall nodes on the walls)."""
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    xy = np.stack([ix.ravel() * h, (iy.ravel() + y_offset) * h], axis=1).astype(np.float64)
+    cls = np.zeros(len(xy), np.uint8)
+    if y_offset == 0.0:
+        cls[(iy.ravel() == 0) | (iy.ravel() == ny - 1)] = WALL
+    H = (ny - 1 + 2 * y_offset) * h
+    return Workload(f"lattice_channel_{nx}x{ny}_o{y_offset:g}", xy, cls, (0.0, 0.0, nx * h, H),
+                    (PERIODIC, PERIODIC, SOLID, SOLID), np.zeros((0, 3)), np.zeros((len(xy), 3)),
+                    np.full(len(xy), h * h), h, {"nx": nx, "ny": ny, "H": H, "y_offset": y_offset})
+
+
+def jittered_periodic(nx: int, ny: int, jitter: float = 0.2, seed: int = 0, h: float = 1.0) -> Workload:
+    """Doubly periodic jittered grid: node (i, j) at h*(i + U(-j, j), j + U(-j, j))."""
+    rng = np.random.default_rng(seed)
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    x = (ix.ravel() + rng.uniform(-jitter, jitter, ix.size)) * h
+    y = (iy.ravel() + rng.uniform(-jitter, jitter, iy.size)) * h
+    lx, ly = nx * h, ny * h
+    xy = np.stack([np.mod(x, lx), np.mod(y, ly)], axis=1)
+    cls = np.zeros(len(xy), np.uint8)
+    return Workload(f"jittered_periodic_{nx}x{ny}_s{seed}", xy, cls, (0.0, 0.0, lx, ly),
+                    (PERIODIC,) * 4, np.zeros((0, 3)), np.zeros((len(xy), 3)),
+                    np.full(len(xy), h * h), h, {"nx": nx, "ny": ny, "jitter": jitter, "seed": seed})
+
+
+def poiseuille_channel(nx: int = 40, ny: int = 50, jitter: float = 0.2, seed: int = 1,
+                       h: float = 1.0) -> Workload:
+    """Periodic-in-x channel with wall nodes on y=0 and y=(ny-1)h.
+
+    Interior nodes are jittered by U(-jitter, jitter)h in both axes; the two
+    wall rows only along x, so they stay on the walls.  40x50 with seed 1 is
+    the plain-MLBM Poiseuille case (2000 nodes)."""
+    rng = np.random.default_rng(seed)
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    ix, iy = ix.ravel(), iy.ravel()
+    jx = rng.uniform(-jitter, jitter, ix.size)
+    jy = rng.uniform(-jitter, jitter, iy.size)
+    wall = (iy == 0) | (iy == ny - 1)
+    jy[wall] = 0.0
+    lx = nx * h
+    x = np.mod((ix + jx) * h, lx)
+    y = (iy + jy) * h
+    xy = np.stack([x, y], axis=1)
+    cls = np.where(wall, WALL, FLUID).astype(np.uint8)
+    area = np.full(len(xy), h * h)
+    area[wall] = 0.5 * h * h
+    return Workload(f"poiseuille_{nx}x{ny}_s{seed}", xy, cls, (0.0, 0.0, lx, (ny - 1) * h),
+                    (PERIODIC, PERIODIC, SOLID, SOLID), np.zeros((0, 3)), np.zeros((len(xy), 3)),
+                    area, h, {"nx": nx, "ny": ny, "jitter": jitter, "seed": seed, "H": (ny - 1) * h})
+
+
+# --------------------------------------------------------------------------
+# Cylinder in a channel
+# --------------------------------------------------------------------------
+def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: float = 4.1,
+           center_d: tuple = (2.0, 2.0), U0: float = 0.05, r_fine: float = 0.37, r_coarse: float = 0.74,
+           fine_band_d: float = 1.5, blend_to_d: float = 4.0, scale: float = 1.0) -> Workload:
+    """Channel length_d*D x height_d*D with a solid cylinder of diameter D.
+
+    Lengths are in units of the reference spacing h_ref=1, so D is the number
+    of spacings across the cylinder.  Scattered Poisson-disk nodes with radius
+    r_fine within fine_band_d*D of the cylinder surface, blended linearly to
+    r_coarse at blend_to_d*D.  The four straight sides carry equilibrium
+    nodes on a regular row spaced r_coarse*1.19 apart: a parabolic inflow and
+    outflow profile with maximum U0 on the left and right, zero velocity on
+    the top and bottom, unit density everywhere.  No nodes closer than half
+    the local radius to the cylinder surface.  `scale` < 1 shrinks D and the
+    channel together for small test cases."""
+    D = D * scale
+    lx, ly = length_d * D, height_d * D
+    cx, cy, R = center_d[0] * D, center_d[1] * D, 0.5 * D
+    # radius field on a grid
+    nrx, nry = int(lx / 2) + 2, int(ly / 2) + 2
+    gx, gy = np.meshgrid(np.linspace(0, lx, nrx), np.linspace(0, ly, nry), indexing="xy")
+    dist = np.hypot(gx - cx, gy - cy) - R
+    t = np.clip((dist - fine_band_d * D) / ((blend_to_d - fine_band_d) * D), 0.0, 1.0)
+    rgrid = r_fine + t * (r_coarse - r_fine)
+    # equilibrium nodes on the four sides
+    hb = r_coarse * 1.19
+    nbx = int(round(lx / hb)); nby = int(round(ly / hb))
+    xs = np.linspace(0.0, lx, nbx + 1)
+    ys = np.linspace(0.0, ly, nby + 1)
+    bottom = np.stack([xs, np.zeros_like(xs)], 1)
+    top = np.stack([xs, np.full_like(xs, ly)], 1)
+    left = np.stack([np.zeros(nby - 1), ys[1:-1]], 1)
+    right = np.stack([np.full(nby - 1, lx), ys[1:-1]], 1)
+    fixed = np.concatenate([bottom, top, left, right], 0)
+    pts = _sample((0.0, 0.0, lx, ly), (0, 0), rgrid, np.array([[cx, cy, R]]), 0.5, fixed, seed,
+                  max_out=int(4 * lx * ly / r_fine ** 2) + len(fixed) + 1000)
+    n = len(pts)
+    nf = len(fixed)
+    cls = np.zeros(n, np.uint8)
+    cls[:nf] = EQ
+    eqv = np.zeros((n, 3))
+    eqv[:nf, 0] = 1.0
+    side_lr = np.zeros(n, bool)
+    side_lr[len(bottom) + len(top):nf] = True
+    yb = pts[:, 1]
+    prof = 4.0 * U0 * yb * (ly - yb) / (ly * ly)
+    eqv[side_lr, 1] = prof[side_lr]
+    # local spacing^2 as node area, normalised to the fluid area
+    fx = np.clip(pts[:, 0] / lx * (nrx - 1), 0, nrx - 1.000001)
+    fy = np.clip(pts[:, 1] / ly * (nry - 1), 0, nry - 1.000001)
+    r_at = rgrid[fy.astype(int), fx.astype(int)]
+    area = r_at ** 2
+    area *= (lx * ly - np.pi * R * R) / area.sum()
+    return Workload(f"karman_D{D:g}_s{seed}", pts, cls, (0.0, 0.0, lx, ly), (OPEN,) * 4,
+                    np.array([[cx, cy, R]]), eqv, area, 1.0,
+                    {"D": D, "U0": U0, "H": ly, "L": lx, "seed": seed, "n_eq": nf})
+
+
+# --------------------------------------------------------------------------
+# Porous box
+# --------------------------------------------------------------------------
+def _rsa_disks(rng, lx, ly, porosity, rmin, rmax, gap, wall_gap, max_tries=400000):
+    """Random sequential addition of non-overlapping disks, periodic in x,
+    kept wall_gap away from the walls at y=0 and y=ly, until the solid area
+    fraction reaches 1 - porosity (or the tries run out)."""
+    target = (1.0 - porosity) * lx * ly
+    disks = []
+    area = 0.0
+    cx = np.zeros(0); cy = np.zeros(0); cr = np.zeros(0)
+    tries = 0
+    while area < target and tries < max_tries:
+        tries += 1
+        r = rng.uniform(rmin, rmax)
+        x = rng.uniform(0.0, lx)
+        y = rng.uniform(r + wall_gap, ly - r - wall_gap)
+        if len(cx):
+            dx = np.abs(cx - x)
+            dx = np.minimum(dx, lx - dx)
+            dy = cy - y
+            if np.any(dx * dx + dy * dy < (cr + r + gap) ** 2):
+                continue
+        disks.append((x, y, r))
+        cx = np.append(cx, x); cy = np.append(cy, y); cr = np.append(cr, r)
+        area += np.pi * r * r
+    return np.array(disks, dtype=np.float64).reshape(-1, 3)
+
+
+def porous(seed: int = 3, n_target: int = 1_000_000, porosity: float = 0.7, rmin: float = 8.0,
+           rmax: float = 16.0, h: float = 1.0, gap: float = 2.0, r_pd: float = 0.84,
+           side: float | None = None) -> Workload:
+    """Square box of random non-overlapping solid disks (radii U(rmin, rmax) in
+    units of h), periodic in x, solid walls at y=0 and y=L.  Wall nodes sit on
+    every solid surface (arc spacing about h); fluid nodes are Poisson-disk
+    samples of radius r_pd*h that keep r_pd*h from the wall nodes.  The side
+    length is chosen so the fluid holds about n_target nodes."""
+    rng = np.random.default_rng(seed)
+    density = 0.68 / (r_pd * h) ** 2          # nodes per unit area for Bridson sampling
+    if side is None:
+        side = float(np.sqrt(n_target / (porosity * density)))
+    lx = ly = side
+    disks = _rsa_disks(rng, lx, ly, porosity, rmin * h, rmax * h, gap * h, 2.0 * h)
+    fixed = []
+    for (x, y, r) in disks:
+        m = max(8, int(round(2 * np.pi * r / h)))
+        ph = rng.uniform(0, 2 * np.pi)
+        a = ph + 2 * np.pi * np.arange(m) / m
+        px = np.mod(x + r * np.cos(a), lx)
+        fixed.append(np.stack([px, y + r * np.sin(a)], 1))
+    nw = int(round(lx / h))
+    xs = (np.arange(nw) + rng.uniform(0, 1)) * (lx / nw)
+    xs = np.mod(xs, lx)
+    fixed.append(np.stack([xs, np.zeros(nw)], 1))
+    fixed.append(np.stack([xs, np.full(nw, ly)], 1))
+    fixed = np.concatenate(fixed, 0)
+    rgrid = np.full((2, 2), r_pd * h)
+    # the top wall row sits at y = ly, outside the half-open sampling box: keep
+    # it as a fixed point by sampling in a box that includes it
+    pts = _sample((0.0, 0.0, lx, ly * (1 + 1e-12) + 1e-9), (1, 0), rgrid, disks, 0.25, fixed, seed,
+                  max_out=int(2.0 * lx * ly * density) + len(fixed) + 1000)
+    n = len(pts)
+    cls = np.zeros(n, np.uint8)
+    cls[:len(fixed)] = WALL
+    fluid_area = lx * ly - np.sum(np.pi * disks[:, 2] ** 2)
+    area = np.full(n, fluid_area / n)
+    phi = fluid_area / (lx * ly)
+    return Workload(f"porous_n{n}_s{seed}", pts, cls, (0.0, 0.0, lx, ly), (PERIODIC, PERIODIC, SOLID, SOLID),
+                    disks, np.zeros((n, 3)), area, h,
+                    {"seed": seed, "porosity": float(phi), "n_disks": len(disks), "L": lx,
+                     "mean_d": float(2 * disks[:, 2].mean()) if len(disks) else 0.0})
+
+
+# --------------------------------------------------------------------------
+# Random arrays (initial perturbations, feature noise); no physics
+# --------------------------------------------------------------------------
+def uniform_noise(shape, seed: int, amp: float = 1.0) -> np.ndarray:
+    """U(-amp, amp) float64 array from a seeded generator."""
+    return np.random.default_rng(seed).uniform(-amp, amp, size=shape)
+
+
+def normal_noise(shape, seed: int, std: float = 1.0) -> np.ndarray:
+    return np.random.default_rng(seed).normal(0.0, std, size=shape)

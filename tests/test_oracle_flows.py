@@ -1,0 +1,267 @@
+"""Flow-level pins of the oracle's MLBM and MLBM1 steps.
+
+* On a regular lattice with streaming distance equal to the spacing the
+  meshless streaming (biquadratic Lagrange on 3x3 stencils, Sec. 2.2) must be
+  the textbook index-shift streaming of Eq. (1): bitwise equal in FP64.
+* MLBM1 on that lattice must be LBM1, Eq. (10)-(11).
+* Closed forms: uniform acceleration, shear-wave decay at nu = (tau - 1/2)/3
+  (Eq. (6)), the Poiseuille profile (steady and transient), the steady
+  momentum balance between body force and wall force, exact mass
+  conservation where streaming is a permutation.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_14789_gb300 import inputs as I
+
+E = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+
+
+def lattice_stream(f, nx, ny):
+    """Eq. (1) on a doubly periodic nx x ny lattice, nodes ordered row-major."""
+    F = f.reshape(ny, nx, 9)
+    G = np.empty_like(F)
+    for k in range(9):
+        G[:, :, k] = np.roll(np.roll(F[:, :, k], E[k, 0], axis=1), E[k, 1], axis=0)
+    return G.reshape(-1, 9)
+
+
+def lattice_stream_halfway_walls(f, nx, ny):
+    """Eq. (1), periodic in x, half-way bounce-back at walls below row 0 and
+    above row ny-1: a population that would leave the fluid comes back
+    reversed at its own node."""
+    F = f.reshape(ny, nx, 9)
+    G = np.empty_like(F)
+    for k in range(9):
+        sh = np.roll(F[:, :, k], E[k, 0], axis=1)
+        if E[k, 1] == 1:
+            G[1:, :, k] = sh[:-1]
+            G[0, :, k] = F[0, :, OPP[k]]
+        elif E[k, 1] == -1:
+            G[:-1, :, k] = sh[1:]
+            G[-1, :, k] = F[-1, :, OPP[k]]
+        else:
+            G[:, :, k] = sh
+    return G.reshape(-1, 9)
+
+
+def collide_all(f, tau_p, tau_m, g):
+    return np.array([O.collide(fi, tau_p, tau_m, *g) for fi in f])
+
+
+def random_state(n, seed, amp=1e-3):
+    rng = np.random.default_rng(seed)
+    rho = 1 + 0.01 * rng.standard_normal(n)
+    ux = 0.02 * rng.standard_normal(n)
+    uy = 0.02 * rng.standard_normal(n)
+    return O.equilibrium(rho, ux, uy) + amp * I.uniform_noise((n, 9), seed + 1)
+
+
+@pytest.mark.parametrize("tau_p,tau_m", [(0.8, 0.8), (0.6, 0.6 + 0.3)])
+def test_regular_lattice_mlbm_is_textbook_lbm_bitwise(tau_p, tau_m):
+    nx, ny = 16, 12
+    w = I.lattice(nx, ny)
+    op = O.Operator(w, K=12, s=1.0).check()
+    assert np.all(op.kind == 1)
+    g = (1e-5, -3e-6)
+    a = random_state(w.n, 3)
+    b = a.copy()
+    for _ in range(30):
+        a = O.bgk_step(op, a, tau_p, g, tau_m)
+        b = collide_all(lattice_stream(b, nx, ny), tau_p, tau_m, g)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("bb_mode", [0, 1])
+def test_regular_channel_with_halfway_walls_is_textbook_bounce_back(bb_mode):
+    nx, ny = 6, 10
+    w = I.lattice_channel(nx, ny, 0.5)
+    # K = 16 holds the 3x3 block centred one row in from each wall row
+    op = O.Operator(w, K=16, s=1.0, bb_mode=bb_mode).check()
+    assert np.all(op.kind == 1)
+    assert op.link.sum() == 2 * 3 * nx
+    assert np.all(op.q[op.link == 1] == 0.5)
+    g = (2e-5, 0.0)
+    a = random_state(w.n, 5)
+    b = a.copy()
+    for _ in range(25):
+        a = O.bgk_step(op, a, 0.7, g)
+        b = collide_all(lattice_stream_halfway_walls(b, nx, ny), 0.7, 0.7, g)
+    assert np.array_equal(a, b)
+
+
+def test_mass_conservation_exact_on_periodic_lattice_and_bounded_on_scattered():
+    w = I.lattice(12, 10)
+    op = O.Operator(w, K=12, s=1.0).check()
+    f = random_state(w.n, 11)
+    m0 = f.sum()
+    for _ in range(100):
+        f = O.bgk_step(op, f, 0.9, (1e-5, 0))
+    assert abs(f.sum() - m0) / m0 < 1e-13
+    # scattered nodes: semi-Lagrangian interpolation is not conservative
+    wj = I.jittered_periodic(12, 10, 0.2, seed=6)
+    opj = O.Operator(wj, K=12, s=1.0).check()
+    f = random_state(wj.n, 11)
+    m0 = f.sum()
+    for _ in range(100):
+        f = O.bgk_step(opj, f, 0.9, (1e-5, 0))
+    drift = abs(f.sum() - m0) / m0
+    assert drift < 1e-3
+
+
+@pytest.mark.parametrize("kind", ["lattice", "jittered"])
+def test_uniform_acceleration(kind):
+    """Uniform state: streaming reproduces constants (partition of unity), so
+    each node gains exactly F per step; the state's velocity after n steps is
+    (n - 1/2) g when starting from the rest equilibrium."""
+    w = I.lattice(8, 8) if kind == "lattice" else I.jittered_periodic(9, 8, 0.25, seed=2)
+    op = O.Operator(w, K=12, s=1.0).check()
+    g = (3e-5, -1e-5)
+    f = O.equilibrium(np.ones(w.n), 0.0, 0.0)
+    for n in range(1, 21):
+        f = O.bgk_step(op, f, 0.75, g)
+        rho, ux, uy = O.macroscopics(f, g)
+        assert np.allclose(rho, 1.0, rtol=0, atol=1e-13)
+        assert np.allclose(ux, (n - 0.5) * g[0], rtol=1e-9, atol=0)
+        assert np.allclose(uy, (n - 0.5) * g[1], rtol=1e-9, atol=0)
+
+
+def test_shear_wave_decay_rate_gives_viscosity():
+    """u_x = U sin(k y) decays as exp(-nu k^2 t) with nu = (tau - 1/2)/3."""
+    L = 32
+    w = I.lattice(4, L)
+    op = O.Operator(w, K=12, s=1.0).check()
+    ky = 2 * np.pi / L
+    y = w.xy[:, 1]
+    for tau in (0.7, 1.0):
+        nu = (tau - 0.5) / 3
+        f = O.equilibrium(np.ones(w.n), 1e-4 * np.sin(ky * y), 0.0)
+        amps = []
+        for t in range(1, 301):
+            f = O.bgk_step(op, f, tau)
+            if t in (100, 300):
+                _, ux, _ = O.macroscopics(f)
+                amps.append(2 * np.mean(ux * np.sin(ky * y)))
+        rate = np.log(amps[0] / amps[1]) / 200
+        # lattice dispersion: relative error O((k h)^2) ~ 4e-2 at L = 32
+        assert abs(rate / (nu * ky * ky) - 1) < 1e-2
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.0])
+def test_steady_poiseuille_bulk_curvature_and_force_balance(tau):
+    nx, ny = 4, 12
+    w = I.lattice_channel(nx, ny, 0.5)
+    op = O.Operator(w, K=12, s=1.0, bb_mode=0).check()
+    g = 1e-5
+    nu = (tau - 0.5) / 3
+    f = O.run_bgk(op, O.equilibrium(np.ones(w.n), 0, 0), tau, (g, 0), 15000)
+    rho, ux, uy = O.macroscopics(f, (g, 0))
+    u = ux.reshape(ny, nx)[:, 0]
+    # the steady parabola solves the bulk update exactly: u'' = -g / nu
+    d2 = u[2:] - 2 * u[1:-1] + u[:-2]
+    assert np.allclose(d2, -g / nu, rtol=1e-9, atol=0)
+    assert np.abs(uy).max() < 1e-9 * np.abs(ux).max()
+    # momentum balance: wall force equals the total body force
+    fx, fy = O.force_bgk(op, f)
+    assert abs(fx / (rho.sum() * g) - 1) < 1e-9
+    assert abs(fy) < 1e-14
+
+
+def test_trt_magic_parameter_gives_exact_poiseuille_with_halfway_walls():
+    """TRT with Lambda = 3/16 (Eq. (5)) puts the half-way bounce-back wall
+    exactly midway between nodes: u(y) = g/(2 nu) y (H - y)."""
+    nx, ny = 4, 12
+    w = I.lattice_channel(nx, ny, 0.5)
+    op = O.Operator(w, K=12, s=1.0, bb_mode=0).check()
+    g, tau_p = 1e-5, 0.8
+    tau_m = 0.5 + (3 / 16) / (tau_p - 0.5)
+    nu = (tau_p - 0.5) / 3
+    f = O.run_bgk(op, O.equilibrium(np.ones(w.n), 0, 0), tau_p, (g, 0), 15000, tau_minus=tau_m)
+    _, ux, _ = O.macroscopics(f, (g, 0))
+    y = w.xy[:, 1]
+    H = w.meta["H"]
+    ua = g / (2 * nu) * y * (H - y)
+    assert np.abs(ux - ua).max() / ua.max() < 1e-9
+
+
+def _poiseuille_transient(y, H, g, nu, t, nmodes=401):
+    u = g / (2 * nu) * y * (H - y)
+    for n in range(1, nmodes, 2):
+        u -= 4 * g * H * H / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * y / H) * \
+            np.exp(-nu * n * n * np.pi ** 2 * t / H ** 2)
+    return u
+
+
+def _jittered_poiseuille_error(nx, ny, model="bgk"):
+    w = I.poiseuille_channel(nx, ny, 0.2, seed=1)
+    op = O.Operator(w, K=12, s=1.0, bb_mode=1).check()
+    H = ny - 1
+    g = 1e-6
+    steps = int(round(2000 * (H / 49) ** 2))
+    if model == "bgk":
+        tau = 0.8
+        f = O.run_bgk(op, O.equilibrium(np.ones(w.n), 0, 0), tau, (g, 0), steps)
+        _, ux, _ = O.macroscopics(f, (g, 0))
+    else:
+        tau = 1.0
+        ru = np.zeros((w.n, 3))
+        ru[:, 0] = 1.0
+        ru = O.run_mlbm1(op, ru, (g, 0), steps)
+        ux = ru[:, 1]
+    nu = (tau - 0.5) / 3
+    return O.relative_l2(ux, _poiseuille_transient(w.xy[:, 1], H, g, nu, steps))
+
+
+@pytest.mark.parametrize("model", ["bgk", "mlbm1"])
+def test_jittered_poiseuille_converges_to_closed_form(model):
+    """Scattered nodes (WLS, interpolated bounce-back with q > 0 near walls):
+    the error against the transient closed form at the same nu t / H^2
+    falls by more than 3x per halving of h (second order)."""
+    e = [_jittered_poiseuille_error(nx, ny, model) for nx, ny in [(10, 13), (20, 25), (40, 50)]]
+    assert e[2] < 3e-3
+    assert e[0] / e[1] > 3.0 and e[1] / e[2] > 3.0
+
+
+def test_mlbm1_on_lattice_is_lbm1():
+    """Eq. (11): rho, u (t+1) = moments of f^eq evaluated at x - e_k."""
+    nx, ny = 10, 8
+    w = I.lattice(nx, ny)
+    op = O.Operator(w, K=12, s=1.0).check()
+    rng = np.random.default_rng(4)
+    ru = np.stack([1 + 0.01 * rng.standard_normal(w.n), 0.02 * rng.standard_normal(w.n),
+                   0.02 * rng.standard_normal(w.n)], 1)
+    a = ru.copy()
+    b = ru.copy()
+    for _ in range(10):
+        a = O.mlbm1_step(op, a)
+        feqs = O.equilibrium(b[:, 0], b[:, 1], b[:, 2])
+        fs = lattice_stream(feqs, nx, ny)
+        rho = fs.sum(1)
+        b = np.stack([rho, fs @ E[:, 0] / rho, fs @ E[:, 1] / rho], 1)
+    assert np.allclose(a, b, rtol=0, atol=1e-15)
+
+
+def test_mlbm1_equals_bgk_at_tau_one_on_lattice_with_force():
+    w = I.lattice_channel(6, 9, 0.5)
+    op = O.Operator(w, K=12, s=1.0, bb_mode=1).check()
+    g = (2e-5, 1e-6)
+    f = O.equilibrium(np.ones(w.n), 0, 0)
+    # start both from the same post-collision state: rho = 1, u = -g/2
+    ru = np.zeros((w.n, 3))
+    ru[:, 0] = 1.0
+    ru[:, 1] = -0.5 * g[0]
+    ru[:, 2] = -0.5 * g[1]
+    f = O.equilibrium(ru[:, 0], ru[:, 1], ru[:, 2])
+    f = np.array([fi + 0.5 * np.array([O.source(k, 1.0, ru[0, 1], ru[0, 2], *g) for k in range(9)])
+                  for fi in f])
+    for _ in range(40):
+        f = O.bgk_step(op, f, 1.0, g)
+        ru = O.mlbm1_step(op, ru, g)
+    rho, ux, uy = O.macroscopics(f, g)
+    assert np.allclose(rho, ru[:, 0], rtol=0, atol=1e-14)
+    # identical up to rounding: BGK forms f - (f - f_eq) where MLBM1 forms f_eq
+    umax = np.abs(ru[:, 1]).max()
+    assert np.abs(ux - ru[:, 1]).max() < 1e-10 * umax
+    assert np.abs(uy - ru[:, 2]).max() < 1e-10 * umax
