@@ -1,0 +1,262 @@
+/*
+ * mlbm.h -- C ABI of the GB300 meshless lattice Boltzmann (MLBM) step.
+ *
+ * The method (Strzelczyk & Matyka, arXiv 2312.14789): D2Q9 populations live
+ * on scattered ("Eulerian") nodes; each time step streams every population
+ * f_k from its departure point x - s e_k (s = streaming distance, decoupled
+ * from the node spacing, Sec. 2.2-2.3), obtained by interpolating the
+ * post-collision field over a stencil of neighbouring nodes (Eq. (12)),
+ * then collides (BGK, or TRT Eq. (3)-(5)).  The tau = 1 variant (MLBM1,
+ * Eq. (14)-(15)) stores only rho and u and interpolates those.
+ *
+ * Conventions for every entry point:
+ *  - All pointers passed in are HOST pointers owned by the caller unless the
+ *    name ends in _device; data is copied on entry, results are written to
+ *    caller-owned host arrays.  The library owns the device memory of a
+ *    context (cudaMalloc at mlbm_init, cudaFree at mlbm_destroy).
+ *  - Node arrays are in the caller's order; the library reorders nodes
+ *    internally (Hilbert curve) and undoes the permutation on output.
+ *  - Units: lattice units (time step 1, population speeds |e_k| in units of
+ *    the streaming distance s); lengths (xy, s, disk radii) in the caller's
+ *    length unit.
+ *  - Errors: every call returns an mlbm_status; on failure a message is
+ *    available from mlbm_last_error() (thread-local).  No call aborts the
+ *    process or traps on the device.
+ *  - Streams: work is issued on the context's stream (default: a stream the
+ *    context creates; see mlbm_set_stream).  Calls that return host data
+ *    synchronise that stream.
+ */
+#ifndef MLBM_H
+#define MLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MLBM_OK = 0,
+    MLBM_E_INVALID = 1,          /* bad argument (null pointer, size, range) */
+    MLBM_E_SINGULAR_STENCIL = 2, /* least-squares normal matrix ill-conditioned (> 1e12) */
+    MLBM_E_CUDA = 3,             /* a CUDA runtime call failed, or no device */
+    MLBM_E_OOM = 4,              /* host or device allocation failed */
+    MLBM_E_DIVERGED = 5,         /* non-finite or non-positive density found */
+    MLBM_E_TIMEOUT = 6,          /* a bounded device wait gave up */
+    MLBM_E_NOT_CONVERGED = 7,    /* run_to_steady reached max_steps */
+    MLBM_E_GEOMETRY = 8,         /* a node lies inside a solid */
+    MLBM_E_IO = 9                /* checkpoint file could not be read or written */
+} mlbm_status;
+
+/* node classes */
+enum { MLBM_NODE_FLUID = 0, MLBM_NODE_WALL = 1, MLBM_NODE_EQ = 2 };
+/* box side types: periodic (the opposite side must be periodic too), solid
+   wall (bounce-back), open (nothing beyond; departure points outside are
+   extrapolated by the fit) */
+enum { MLBM_SIDE_PERIODIC = 0, MLBM_SIDE_SOLID = 1, MLBM_SIDE_OPEN = 2 };
+/* bounce-back rule on links whose departure segment enters a solid */
+enum { MLBM_BB_SIMPLE = 0, MLBM_BB_INTERPOLATED = 1 };
+/* collision model */
+enum { MLBM_MODEL_BGK = 0, MLBM_MODEL_TAU1 = 1 };
+
+typedef struct mlbm_stencils mlbm_stencils;
+typedef struct mlbm_ctx mlbm_ctx;
+
+/* Node set.  xy[n][2] positions; node_class[n] in MLBM_NODE_*; eq_values
+   [n][3] = (rho_b, ux_b, uy_b) used only for MLBM_NODE_EQ nodes (may be NULL
+   when there are none); area[n] node areas in length units^2 (NULL: 1), used
+   by the area-weighted observables and the wall force. */
+typedef struct {
+    int64_t n;
+    const double* xy;
+    const uint8_t* node_class;
+    const double* eq_values;
+    const double* area;
+} mlbm_nodes;
+
+/* Box [x0, x1] x [y0, y1] with side types (left, right, bottom, top) and
+   solid disks[n_disks][3] = (cx, cy, r).  Disks near a periodic side also
+   act through their periodic images. */
+typedef struct {
+    double x0, y0, x1, y1;
+    int side[4];
+    int n_disks;
+    const double* disks;
+} mlbm_geometry;
+
+/* ---------------------------------------------------------------- stencils */
+/*
+ * Build everything the step needs for one node set and one streaming
+ * distance s (Sec. 2.2; the precomputation the paper does once per node set):
+ *  - K nearest nodes of every node, itself included, ordered by (squared
+ *    distance, caller's node id); offsets use the minimum image across
+ *    periodic sides (Sec. 3.2: periodic stencil search);
+ *  - the 6 x K weighted least-squares matrix M = (P^T W P)^-1 P^T W of a
+ *    quadratic fit, Gaussian weights exp(-r^2 / sigma^2) with
+ *    sigma = sigma_factor * (largest stencil offset), solved in FP64
+ *    (Householder QR) and stored in FP32 scaled to units of s;
+ *  - when use_lagrange != 0, nodes whose stencil holds an axis-aligned 3x3
+ *    block that contains all their departure points use biquadratic
+ *    Lagrange interpolation instead (Sec. 2.2, regular parts of hybrid
+ *    node sets);
+ *  - bounce-back links: directions whose departure segment from x to
+ *    x - s e_k enters a solid, with the entry fraction q; bb_mode selects
+ *    simple bounce-back f_k = f_{k'}^post(x) (Sec. 3.1) or interpolated
+ *    bounce-back at x + (1 - 2q) s e_k (Eq. (22) when q = 0);
+ *  - a Hilbert-curve node order.
+ * K: 6..32 and a multiple of 4 (9..32 with use_lagrange); s > 0;
+ * sigma_factor > 0.  Host-only work (no GPU needed).  *out is owned by the
+ * caller and released with mlbm_stencils_free.
+ * Errors: MLBM_E_INVALID, MLBM_E_SINGULAR_STENCIL, MLBM_E_GEOMETRY, MLBM_E_OOM.
+ */
+mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
+                                double sigma_factor, int bb_mode, int use_lagrange, mlbm_stencils** out);
+
+void mlbm_stencils_free(mlbm_stencils* st);
+
+typedef struct {
+    int64_t n;            /* nodes */
+    int K;
+    double s;
+    int64_t n_wls;        /* nodes interpolated by the least-squares fit */
+    int64_t n_lagrange;   /* nodes interpolated by biquadratic Lagrange */
+    int64_t n_eq;         /* equilibrium-overwrite nodes */
+    int64_t n_link_nodes; /* nodes with at least one bounce-back link */
+    int64_t n_links;      /* bounce-back links */
+    double build_seconds; /* host time spent in mlbm_build_stencils */
+} mlbm_stencil_info;
+
+mlbm_status mlbm_stencils_info(const mlbm_stencils* st, mlbm_stencil_info* info);
+
+/*
+ * Copy the stencil data out in the caller's node order (for inspection and
+ * tests; any pointer may be NULL to skip that array):
+ *   idx[n][K]     neighbour node ids (caller's ids), search order
+ *   M[n][6][K]    FP64 least-squares matrix in units of s (zero for other kinds)
+ *   kind[n]       0 least squares, 1 Lagrange, 2 equilibrium node
+ *   link_mask[n]  bit k set when direction k (1..8) is a bounce-back link
+ *   q[n][9]       entry fractions of the links (0 elsewhere)
+ *   lag_h[n]      Lagrange block spacing h (0 for other kinds)
+ *   lag_center[n] block centre as a D2Q9 direction index m (c = x + h e_m)
+ */
+mlbm_status mlbm_stencils_export(const mlbm_stencils* st, int64_t* idx, double* M, int32_t* kind,
+                                 int32_t* link_mask, double* q, double* lag_h, int32_t* lag_center);
+
+/* ----------------------------------------------------------------- context */
+typedef struct {
+    int model;        /* MLBM_MODEL_BGK or MLBM_MODEL_TAU1 */
+    double tau;       /* tau+ (viscosity nu = (tau - 1/2)/3, Eq. (6)); must be 1 for TAU1 */
+    double tau_minus; /* TRT tau-; <= 0 means tau_minus = tau (BGK) */
+    double gx, gy;    /* body acceleration (lattice units), second-order source */
+} mlbm_params;
+
+/*
+ * Create a context on the current CUDA device: uploads the stencils, allocates
+ * two state buffers and sets the state at t = 0 to the equilibrium of
+ * (rho0, u0) (rho0 NULL: 1; u0 NULL: 0; u0 is [n][2]).  For MLBM_MODEL_BGK the
+ * state is the post-collision populations f_k^post (FP32, stored minus the
+ * weights omega_k); for MLBM_MODEL_TAU1 it is (rho, ux, uy).
+ * Errors: MLBM_E_INVALID, MLBM_E_CUDA, MLBM_E_OOM.
+ */
+mlbm_status mlbm_init(mlbm_ctx** out, const mlbm_stencils* st, const mlbm_params* p, const double* rho0,
+                      const double* u0);
+
+void mlbm_destroy(mlbm_ctx* ctx);
+
+/* Use a caller-owned cudaStream_t (NULL: the context's own stream). */
+mlbm_status mlbm_set_stream(mlbm_ctx* ctx, void* stream);
+
+/* Replace the state: BGK f[n][9] post-collision populations; TAU1 rho_u[n][3]. */
+mlbm_status mlbm_set_populations(mlbm_ctx* ctx, const double* f);
+mlbm_status mlbm_set_fields(mlbm_ctx* ctx, const double* rho_u);
+/* Read the state back (BGK: f[n][9]; TAU1: rho_u[n][3]). */
+mlbm_status mlbm_get_populations(mlbm_ctx* ctx, double* f);
+mlbm_status mlbm_get_fields(mlbm_ctx* ctx, double* rho_u);
+
+/*
+ * Advance n_steps time steps (one fused kernel launch per step: gather,
+ * interpolate to the departure points, bounce-back, moments, collision,
+ * write the other buffer).  Asynchronous on the context's stream.
+ */
+mlbm_status mlbm_step(mlbm_ctx* ctx, int64_t n_steps);
+
+/* Steps taken since mlbm_init (or the last state replacement / load). */
+int64_t mlbm_step_count(const mlbm_ctx* ctx);
+
+/*
+ * Density and velocity of the current state at every node (caller's order):
+ * rho[n], u[n][2].  For BGK these are the moments the last collision used
+ * (rho = sum f, rho u = sum f e - rho g / 2).  Either pointer may be NULL.
+ */
+mlbm_status mlbm_macroscopics(mlbm_ctx* ctx, double* rho, double* u);
+
+/*
+ * Force on all solids (momentum exchange over the bounce-back links, per unit
+ * lattice area times area_x / s^2), as exchanged in the next streaming step
+ * from the current state.  cd, cl = 2 F / (rho_ref u_ref^2 L_lb) with
+ * L_lb = ref_length / s, rho_ref = 1.  Any output pointer may be NULL.
+ */
+mlbm_status mlbm_drag_lift(mlbm_ctx* ctx, double ref_length, double u_ref, double* fx, double* fy,
+                           double* cd, double* cl);
+
+/*
+ * Porous-media observables (Sec. 3.2, Eq. (23), (25)) over non-equilibrium
+ * nodes, FP64 area-weighted sums with a fixed summation order:
+ *   u_superficial = sum(u_x A) / box area,  u_intrinsic = sum(u_x A) / sum(A),
+ *   k = nu u_superficial / |g| with nu = (tau - 1/2)/3 (Darcy),
+ *   tortuosity = sum(|u| A) / sum(u_x A).
+ * Any output pointer may be NULL.  k is 0 when g = 0.
+ */
+mlbm_status mlbm_permeability(mlbm_ctx* ctx, double* k, double* u_superficial, double* u_intrinsic,
+                              double* tortuosity);
+
+/*
+ * Step until the relative change of the velocity field over `window` steps,
+ * ||u(t) - u(t - window)||_2 / (window ||u(t)||_2), falls below tol (checked
+ * every `window` steps), or max_steps is reached (MLBM_E_NOT_CONVERGED).
+ * *steps_taken (may be NULL) receives the steps advanced by this call.
+ * Returns MLBM_E_DIVERGED on a non-finite velocity norm.
+ */
+mlbm_status mlbm_run_to_steady(mlbm_ctx* ctx, double tol, int64_t window, int64_t max_steps,
+                               int64_t* steps_taken);
+
+/* Checkpoint the state, step count and parameters to a file / restore them
+   into a context built from the same stencils (node count and K checked). */
+mlbm_status mlbm_save(mlbm_ctx* ctx, const char* path);
+mlbm_status mlbm_load(mlbm_ctx* ctx, const char* path);
+
+/* Average duration (ms) of the fused step kernels launched by the last
+   mlbm_step call, measured with CUDA events on the context's stream when
+   timing is enabled (mlbm_set_timing(ctx, 1)); -1 when not measured. */
+mlbm_status mlbm_set_timing(mlbm_ctx* ctx, int enable);
+double mlbm_last_step_ms(const mlbm_ctx* ctx);
+
+/* ------------------------------------------------ device-level reductions */
+/*
+ * Area-weighted FP64 sums over n nodes of device arrays (FP32): rho[n],
+ * ux[n], uy[n], area[n], and mask[n] (uint8, nodes with mask 0 are skipped;
+ * NULL: all).  out[6] (device, FP64) receives
+ *   sum A, sum rho A, sum ux A, sum uy A, sum |u| A, sum |u|^2 A.
+ * Two kernels: per-block partial sums into scratch (device, FP64, at least
+ * mlbm_reduce_scratch_doubles(n) entries), then one block adds the partials
+ * in a fixed order, so the result is bitwise reproducible.  Asynchronous on
+ * `stream` (a cudaStream_t, NULL = default stream).
+ * Errors: MLBM_E_INVALID (null pointers, n < 0, scratch too small), MLBM_E_CUDA.
+ */
+int64_t mlbm_reduce_scratch_doubles(int64_t n);
+mlbm_status mlbm_reduce_fields_device(const float* rho, const float* ux, const float* uy, const float* area,
+                                      const uint8_t* mask, int64_t n, double* scratch, int64_t scratch_len,
+                                      double* out, void* stream);
+
+/* Last error message of this thread ("" when none). */
+const char* mlbm_last_error(void);
+
+/* Library version string. */
+const char* mlbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLBM_H */

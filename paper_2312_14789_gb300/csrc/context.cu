@@ -1,0 +1,534 @@
+// C-ABI glue: simulation contexts, state I/O, the step loop and observables.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mlbm_internal.h"
+
+namespace mlbm {
+
+thread_local std::string g_last_error;
+
+mlbm_status set_error(mlbm_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+void clear_error() { g_last_error.clear(); }
+
+}  // namespace mlbm
+
+using namespace mlbm;
+
+struct mlbm_ctx {
+    int device = 0;
+    mlbm_params params{};
+    int64_t n = 0, n_pad = 0;
+    int K = 0;
+    double s = 1.0, box_area = 1.0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    // stencil data on the device
+    int4* idx = nullptr;
+    float4* M = nullptr;
+    uint8_t* meta = nullptr;
+    float* lag_r = nullptr;
+    int* link_slot = nullptr;
+    dev::LinkRec* links = nullptr;
+    float4* eqv = nullptr;
+    int* perm = nullptr;
+    float* area = nullptr;
+    float* area_over_s2 = nullptr;
+    uint8_t* mask = nullptr;
+    int* link_nodes = nullptr;
+    int n_link_nodes = 0;
+    // state
+    float4* f8[2] = {nullptr, nullptr};
+    float* f0[2] = {nullptr, nullptr};
+    float4* ruv[2] = {nullptr, nullptr};
+    int cur = 0;
+    // work
+    float *rho = nullptr, *ux = nullptr, *uy = nullptr, *px = nullptr, *py = nullptr;
+    double* io = nullptr;
+    double* scratch = nullptr;
+    int64_t scratch_len = 0;
+    double* small = nullptr;
+    int64_t steps = 0;
+    bool timing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double last_ms = -1.0;
+    int block = 256;
+    dev::Stencil S{};
+    dev::Collide C{};
+    std::vector<void*> allocations;
+};
+
+namespace {
+
+#define MLBM_CUDA(call)                                                                                      \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess)                                                                               \
+            return set_error(MLBM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+template <class T>
+mlbm_status dalloc(mlbm_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return set_error(e == cudaErrorMemoryAllocation ? MLBM_E_OOM : MLBM_E_CUDA,
+                         std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->allocations.push_back(q);
+    *p = static_cast<T*>(q);
+    return MLBM_OK;
+}
+
+#define MLBM_TRY(expr)                       \
+    do {                                     \
+        mlbm_status s_ = (expr);             \
+        if (s_ != MLBM_OK) return s_;        \
+    } while (0)
+
+mlbm_status upload(mlbm_ctx* c, void* dst, const void* src, size_t bytes) {
+    MLBM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return MLBM_OK;
+}
+
+void set_collide(mlbm_ctx* c) {
+    const double tp = c->params.tau;
+    const double tm = c->params.tau_minus > 0 ? c->params.tau_minus : tp;
+    c->C.omega_p = (float)(1.0 / tp);
+    c->C.omega_m = (float)(1.0 / tm);
+    c->C.src_p = (float)(1.0 - 0.5 / tp);
+    c->C.src_m = (float)(1.0 - 0.5 / tm);
+    c->C.ax = (float)c->params.gx;
+    c->C.ay = (float)c->params.gy;
+}
+
+mlbm_status check_params(const mlbm_params* p) {
+    if (p->model != MLBM_MODEL_BGK && p->model != MLBM_MODEL_TAU1) return set_error(MLBM_E_INVALID, "bad model");
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return set_error(MLBM_E_INVALID, "tau must be > 1/2");
+    if (p->tau_minus > 0 && !(p->tau_minus > 0.5)) return set_error(MLBM_E_INVALID, "tau_minus must be > 1/2");
+    if (p->model == MLBM_MODEL_TAU1 && (p->tau != 1.0 || (p->tau_minus > 0 && p->tau_minus != 1.0)))
+        return set_error(MLBM_E_INVALID, "the tau = 1 model needs tau = tau_minus = 1");
+    if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) return set_error(MLBM_E_INVALID, "non-finite body force");
+    return MLBM_OK;
+}
+
+mlbm_status sync(mlbm_ctx* c) {
+    MLBM_CUDA(cudaStreamSynchronize(c->stream));
+    return MLBM_OK;
+}
+
+mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, const double* rho0, const double* u0) {
+    const HostStencils& H = st->h;
+    MLBM_CUDA(cudaGetDevice(&c->device));
+    MLBM_CUDA(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    c->stream = c->own_stream;
+    c->params = *p;
+    c->n = H.n;
+    c->K = H.K;
+    c->s = H.s;
+    c->box_area = H.box_area;
+    c->n_pad = (H.n + 127) / 128 * 128;
+    const int64_t n = H.n, np = c->n_pad;
+    const int K = H.K, Kq = K / 4;
+    // ---- host-side device layout
+    std::vector<int32_t> hidx((size_t)Kq * np * 4, 0);
+    std::vector<float> hM((size_t)6 * Kq * np * 4, 0.f);
+    std::vector<uint8_t> hmeta(np, 0), hmask(np, 0);
+    std::vector<float> hlag(np, 0.f), harea(np, 0.f), has2(np, 0.f);
+    std::vector<int> hslot(np, -1), hperm(np, 0), hlinknodes;
+    std::vector<dev::LinkRec> hlinks;
+    std::vector<float4> heqv(np, make_float4(0, 0, 0, 0));
+    for (int64_t q = 0; q < n; ++q) {
+        const uint8_t kind = H.kind[q];
+        const uint16_t lm = H.link_mask[q];
+        hmeta[q] = (uint8_t)(kind | (lm ? 4 : 0) | (H.center[q] << 4));
+        hmask[q] = kind != kKindEq;
+        hperm[q] = (int)H.perm[q];
+        harea[q] = (float)H.area[q];
+        has2[q] = (float)(H.area[q] / (H.s * H.s));
+        if (kind == kKindWls) {
+            for (int j = 0; j < K; ++j) {
+                hidx[(((size_t)(j / 4)) * np + q) * 4 + (j % 4)] = H.idx[(size_t)q * K + j];
+                for (int a = 0; a < 6; ++a)
+                    hM[(((size_t)(a * Kq + j / 4)) * np + q) * 4 + (j % 4)] = (float)H.M[((size_t)q * 6 + a) * K + j];
+            }
+        } else if (kind == kKindLagrange) {
+            for (int b = 0; b < 9; ++b) {
+                const int j = H.lag_slot[(size_t)q * 9 + b];
+                hidx[(((size_t)(b / 4)) * np + q) * 4 + (b % 4)] = H.idx[(size_t)q * K + j];
+            }
+            hlag[q] = (float)(H.s / H.lag_h[q]);
+        } else {
+            heqv[q] = make_float4((float)(H.eqv[q * 3] - 1.0), (float)H.eqv[q * 3 + 1], (float)H.eqv[q * 3 + 2], 0.f);
+        }
+        if (lm) {
+            dev::LinkRec r{};
+            r.mask = lm;
+            for (int k = 1; k < 9; ++k) r.t[k - 1] = (float)(1.0 - 2.0 * H.q[(size_t)q * 9 + k]);
+            hslot[q] = (int)hlinks.size();
+            hlinks.push_back(r);
+            hlinknodes.push_back((int)q);
+        }
+    }
+    c->n_link_nodes = (int)hlinknodes.size();
+    // ---- device buffers
+    MLBM_TRY(dalloc(c, &c->idx, (size_t)Kq * np));
+    MLBM_TRY(dalloc(c, &c->M, (size_t)6 * Kq * np));
+    MLBM_TRY(dalloc(c, &c->meta, np));
+    MLBM_TRY(dalloc(c, &c->mask, np));
+    MLBM_TRY(dalloc(c, &c->lag_r, np));
+    MLBM_TRY(dalloc(c, &c->link_slot, np));
+    MLBM_TRY(dalloc(c, &c->links, hlinks.size()));
+    MLBM_TRY(dalloc(c, &c->link_nodes, hlinknodes.size()));
+    MLBM_TRY(dalloc(c, &c->eqv, np));
+    MLBM_TRY(dalloc(c, &c->perm, np));
+    MLBM_TRY(dalloc(c, &c->area, np));
+    MLBM_TRY(dalloc(c, &c->area_over_s2, np));
+    for (int b = 0; b < 2; ++b) {
+        if (p->model == MLBM_MODEL_BGK) {
+            MLBM_TRY(dalloc(c, &c->f8[b], (size_t)2 * np));
+            MLBM_TRY(dalloc(c, &c->f0[b], np));
+        } else {
+            MLBM_TRY(dalloc(c, &c->ruv[b], np));
+        }
+    }
+    MLBM_TRY(dalloc(c, &c->rho, np));
+    MLBM_TRY(dalloc(c, &c->ux, np));
+    MLBM_TRY(dalloc(c, &c->uy, np));
+    MLBM_TRY(dalloc(c, &c->px, np));
+    MLBM_TRY(dalloc(c, &c->py, np));
+    MLBM_TRY(dalloc(c, &c->io, (size_t)9 * np));
+    c->scratch_len = std::max<int64_t>(6 * reduce_blocks(np), 2 * force_blocks(c->n_link_nodes));
+    MLBM_TRY(dalloc(c, &c->scratch, c->scratch_len));
+    MLBM_TRY(dalloc(c, &c->small, 16));
+    MLBM_TRY(upload(c, c->idx, hidx.data(), hidx.size() * 4));
+    MLBM_TRY(upload(c, c->M, hM.data(), hM.size() * 4));
+    MLBM_TRY(upload(c, c->meta, hmeta.data(), np));
+    MLBM_TRY(upload(c, c->mask, hmask.data(), np));
+    MLBM_TRY(upload(c, c->lag_r, hlag.data(), np * 4));
+    MLBM_TRY(upload(c, c->link_slot, hslot.data(), np * 4));
+    if (!hlinks.empty()) MLBM_TRY(upload(c, c->links, hlinks.data(), hlinks.size() * sizeof(dev::LinkRec)));
+    if (!hlinknodes.empty()) MLBM_TRY(upload(c, c->link_nodes, hlinknodes.data(), hlinknodes.size() * 4));
+    MLBM_TRY(upload(c, c->eqv, heqv.data(), np * sizeof(float4)));
+    MLBM_TRY(upload(c, c->perm, hperm.data(), np * 4));
+    MLBM_TRY(upload(c, c->area, harea.data(), np * 4));
+    MLBM_TRY(upload(c, c->area_over_s2, has2.data(), np * 4));
+    MLBM_CUDA(cudaMemsetAsync(c->px, 0, np * 4, c->stream));
+    MLBM_CUDA(cudaMemsetAsync(c->py, 0, np * 4, c->stream));
+    for (int b = 0; b < 2; ++b) {
+        if (c->f8[b]) {
+            MLBM_CUDA(cudaMemsetAsync(c->f8[b], 0, (size_t)2 * np * sizeof(float4), c->stream));
+            MLBM_CUDA(cudaMemsetAsync(c->f0[b], 0, np * 4, c->stream));
+        }
+        if (c->ruv[b]) MLBM_CUDA(cudaMemsetAsync(c->ruv[b], 0, np * sizeof(float4), c->stream));
+    }
+    c->S.n = (int)n;
+    c->S.n_pad = (int)np;
+    c->S.K = K;
+    c->S.Kq = Kq;
+    c->S.bb_mode = H.bb_mode;
+    c->S.idx = c->idx;
+    c->S.M = c->M;
+    c->S.meta = c->meta;
+    c->S.lag_r = c->lag_r;
+    c->S.link_slot = c->link_slot;
+    c->S.links = c->links;
+    c->S.eqv = c->eqv;
+    set_collide(c);
+    // ---- initial state
+    std::vector<double> ru((size_t)n * 3);
+    for (int64_t i = 0; i < n; ++i) {
+        ru[i * 3] = rho0 ? rho0[i] : 1.0;
+        ru[i * 3 + 1] = u0 ? u0[2 * i] : 0.0;
+        ru[i * 3 + 2] = u0 ? u0[2 * i + 1] : 0.0;
+    }
+    MLBM_TRY(upload(c, c->io, ru.data(), ru.size() * 8));
+    if (p->model == MLBM_MODEL_BGK) {
+        MLBM_CUDA(launch_set_bgk_equilibrium((int)n, c->perm, c->io, c->f8[0], c->f0[0], c->stream));
+    } else {
+        MLBM_CUDA(launch_set_tau1((int)n, c->perm, c->io, c->ruv[0], c->stream));
+    }
+    MLBM_CUDA(cudaEventCreate(&c->ev0));
+    MLBM_CUDA(cudaEventCreate(&c->ev1));
+    return sync(c);
+}
+
+void free_ctx(mlbm_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void* p : c->allocations) cudaFree(p);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+mlbm_status fields_to_work(mlbm_ctx* c, double* ru_dev_or_null) {
+    const int n = (int)c->n;
+    MLBM_CUDA(launch_macroscopics(c->params.model, n, c->perm, c->f8[c->cur], c->f0[c->cur], c->ruv[c->cur],
+                                  (float)c->params.gx, (float)c->params.gy, c->rho, c->ux, c->uy, ru_dev_or_null,
+                                  c->stream));
+    return MLBM_OK;
+}
+
+}  // namespace
+
+
+extern "C" {
+
+const char* mlbm_last_error(void) { return mlbm::g_last_error.c_str(); }
+
+const char* mlbm_version(void) { return "mlbm-gb300 0.1 (sm_103a)"; }
+
+mlbm_status mlbm_init(mlbm_ctx** out, const mlbm_stencils* st, const mlbm_params* p, const double* rho0,
+                      const double* u0) {
+    clear_error();
+    if (!out || !st || !p) return set_error(MLBM_E_INVALID, "init: NULL argument");
+    *out = nullptr;
+    MLBM_TRY(check_params(p));
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        (void)cudaGetLastError();
+        return set_error(MLBM_E_CUDA, std::string("init: no CUDA device (") + cudaGetErrorString(e) + ")");
+    }
+    auto* c = new (std::nothrow) mlbm_ctx;
+    if (!c) return set_error(MLBM_E_OOM, "init: out of host memory");
+    mlbm_status s = do_init(c, st, p, rho0, u0);
+    if (s != MLBM_OK) {
+        std::string msg = g_last_error;
+        free_ctx(c);
+        return set_error(s, msg);
+    }
+    *out = c;
+    return MLBM_OK;
+}
+
+void mlbm_destroy(mlbm_ctx* ctx) { free_ctx(ctx); }
+
+mlbm_status mlbm_set_stream(mlbm_ctx* c, void* stream) {
+    if (!c) return set_error(MLBM_E_INVALID, "set_stream: NULL context");
+    MLBM_CUDA(cudaStreamSynchronize(c->stream));
+    c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_set_populations(mlbm_ctx* c, const double* f) {
+    if (!c || !f) return set_error(MLBM_E_INVALID, "set_populations: NULL argument");
+    if (c->params.model != MLBM_MODEL_BGK) return set_error(MLBM_E_INVALID, "set_populations: BGK contexts only");
+    MLBM_TRY(upload(c, c->io, f, (size_t)c->n * 9 * 8));
+    MLBM_CUDA(launch_set_bgk((int)c->n, c->perm, c->io, c->f8[c->cur], c->f0[c->cur], c->stream));
+    c->steps = 0;
+    return sync(c);
+}
+
+mlbm_status mlbm_set_fields(mlbm_ctx* c, const double* ru) {
+    if (!c || !ru) return set_error(MLBM_E_INVALID, "set_fields: NULL argument");
+    MLBM_TRY(upload(c, c->io, ru, (size_t)c->n * 3 * 8));
+    if (c->params.model == MLBM_MODEL_BGK)
+        MLBM_CUDA(launch_set_bgk_equilibrium((int)c->n, c->perm, c->io, c->f8[c->cur], c->f0[c->cur], c->stream));
+    else
+        MLBM_CUDA(launch_set_tau1((int)c->n, c->perm, c->io, c->ruv[c->cur], c->stream));
+    c->steps = 0;
+    return sync(c);
+}
+
+mlbm_status mlbm_get_populations(mlbm_ctx* c, double* f) {
+    if (!c || !f) return set_error(MLBM_E_INVALID, "get_populations: NULL argument");
+    if (c->params.model != MLBM_MODEL_BGK) return set_error(MLBM_E_INVALID, "get_populations: BGK contexts only");
+    MLBM_CUDA(launch_get_bgk((int)c->n, c->perm, c->f8[c->cur], c->f0[c->cur], c->io, c->stream));
+    MLBM_CUDA(cudaMemcpyAsync(f, c->io, (size_t)c->n * 9 * 8, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+mlbm_status mlbm_get_fields(mlbm_ctx* c, double* ru) {
+    if (!c || !ru) return set_error(MLBM_E_INVALID, "get_fields: NULL argument");
+    MLBM_TRY(fields_to_work(c, c->io));
+    MLBM_CUDA(cudaMemcpyAsync(ru, c->io, (size_t)c->n * 3 * 8, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+mlbm_status mlbm_step(mlbm_ctx* c, int64_t n_steps) {
+    if (!c) return set_error(MLBM_E_INVALID, "step: NULL context");
+    if (n_steps < 0) return set_error(MLBM_E_INVALID, "step: negative step count");
+    if (n_steps == 0) return MLBM_OK;
+    if (c->timing) MLBM_CUDA(cudaEventRecord(c->ev0, c->stream));
+    for (int64_t t = 0; t < n_steps; ++t) {
+        const int a = c->cur, b = c->cur ^ 1;
+        if (c->params.model == MLBM_MODEL_BGK)
+            MLBM_CUDA(launch_bgk_step(c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->C, c->block, c->stream));
+        else
+            MLBM_CUDA(launch_tau1_step(c->S, c->ruv[a], c->ruv[b], c->C, c->block, c->stream));
+        c->cur = b;
+    }
+    c->steps += n_steps;
+    if (c->timing) {
+        MLBM_CUDA(cudaEventRecord(c->ev1, c->stream));
+        MLBM_CUDA(cudaEventSynchronize(c->ev1));
+        float ms = 0.f;
+        MLBM_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        c->last_ms = ms / (double)n_steps;
+    }
+    return MLBM_OK;
+}
+
+int64_t mlbm_step_count(const mlbm_ctx* c) { return c ? c->steps : -1; }
+
+mlbm_status mlbm_set_timing(mlbm_ctx* c, int enable) {
+    if (!c) return set_error(MLBM_E_INVALID, "set_timing: NULL context");
+    c->timing = enable != 0;
+    c->last_ms = -1.0;
+    return MLBM_OK;
+}
+
+double mlbm_last_step_ms(const mlbm_ctx* c) { return c ? c->last_ms : -1.0; }
+
+mlbm_status mlbm_macroscopics(mlbm_ctx* c, double* rho, double* u) {
+    if (!c) return set_error(MLBM_E_INVALID, "macroscopics: NULL context");
+    MLBM_TRY(fields_to_work(c, c->io));
+    std::vector<double> ru((size_t)c->n * 3);
+    MLBM_CUDA(cudaMemcpyAsync(ru.data(), c->io, ru.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    MLBM_TRY(sync(c));
+    for (int64_t i = 0; i < c->n; ++i) {
+        if (rho) rho[i] = ru[i * 3];
+        if (u) {
+            u[2 * i] = ru[i * 3 + 1];
+            u[2 * i + 1] = ru[i * 3 + 2];
+        }
+    }
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_drag_lift(mlbm_ctx* c, double ref_length, double u_ref, double* fx, double* fy, double* cd,
+                           double* cl) {
+    if (!c) return set_error(MLBM_E_INVALID, "drag_lift: NULL context");
+    double h[2] = {0, 0};
+    if (c->n_link_nodes > 0) {
+        MLBM_CUDA(launch_force(c->S, c->params.model, c->n_link_nodes, c->link_nodes, c->area_over_s2,
+                               c->f8[c->cur], c->ruv[c->cur], c->C, c->scratch, c->small, c->stream));
+        MLBM_CUDA(cudaMemcpyAsync(h, c->small, 16, cudaMemcpyDeviceToHost, c->stream));
+        MLBM_TRY(sync(c));
+    }
+    if (fx) *fx = h[0];
+    if (fy) *fy = h[1];
+    const double L = ref_length / c->s;
+    const double den = u_ref * u_ref * L;
+    if (cd) *cd = den != 0 ? 2.0 * h[0] / den : 0.0;
+    if (cl) *cl = den != 0 ? 2.0 * h[1] / den : 0.0;
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_permeability(mlbm_ctx* c, double* k, double* us, double* ui, double* tort) {
+    if (!c) return set_error(MLBM_E_INVALID, "permeability: NULL context");
+    MLBM_TRY(fields_to_work(c, nullptr));
+    MLBM_CUDA(launch_reduce_fields(c->rho, c->ux, c->uy, c->area, c->mask, c->n, c->scratch, c->small, c->stream));
+    double h[6];
+    MLBM_CUDA(cudaMemcpyAsync(h, c->small, 48, cudaMemcpyDeviceToHost, c->stream));
+    MLBM_TRY(sync(c));
+    const double sup = h[2] / c->box_area;
+    const double gmag = std::sqrt(c->params.gx * c->params.gx + c->params.gy * c->params.gy);
+    const double nu = (c->params.tau - 0.5) / 3.0;
+    if (us) *us = sup;
+    if (ui) *ui = h[0] != 0 ? h[2] / h[0] : 0.0;
+    if (k) *k = gmag > 0 ? nu * sup / gmag : 0.0;
+    if (tort) *tort = h[2] != 0 ? h[4] / h[2] : 0.0;
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_run_to_steady(mlbm_ctx* c, double tol, int64_t window, int64_t max_steps, int64_t* taken) {
+    if (!c) return set_error(MLBM_E_INVALID, "run_to_steady: NULL context");
+    if (!(tol > 0) || window < 1 || max_steps < 0) return set_error(MLBM_E_INVALID, "run_to_steady: bad arguments");
+    int64_t done = 0;
+    if (taken) *taken = 0;
+    // reference snapshot u(t0)
+    MLBM_TRY(fields_to_work(c, nullptr));
+    MLBM_CUDA(launch_change(c->ux, c->uy, c->px, c->py, c->mask, c->n, c->scratch, c->small, c->stream));
+    while (done < max_steps) {
+        const int64_t w = std::min(window, max_steps - done);
+        MLBM_TRY(mlbm_step(c, w));
+        done += w;
+        if (taken) *taken = done;
+        MLBM_TRY(fields_to_work(c, nullptr));
+        MLBM_CUDA(launch_change(c->ux, c->uy, c->px, c->py, c->mask, c->n, c->scratch, c->small, c->stream));
+        double h[2];
+        MLBM_CUDA(cudaMemcpyAsync(h, c->small, 16, cudaMemcpyDeviceToHost, c->stream));
+        MLBM_TRY(sync(c));
+        if (!std::isfinite(h[0]) || !std::isfinite(h[1]))
+            return set_error(MLBM_E_DIVERGED, "run_to_steady: non-finite velocity field");
+        const double delta = h[1] > 0 ? std::sqrt(h[0] / h[1]) / (double)w : 0.0;
+        if (w == window && delta < tol) return MLBM_OK;
+    }
+    return set_error(MLBM_E_NOT_CONVERGED, "run_to_steady: max_steps reached");
+}
+
+mlbm_status mlbm_save(mlbm_ctx* c, const char* path) {
+    if (!c || !path) return set_error(MLBM_E_INVALID, "save: NULL argument");
+    const int per = c->params.model == MLBM_MODEL_BGK ? 9 : 3;
+    std::vector<double> buf((size_t)c->n * per);
+    MLBM_TRY(per == 9 ? mlbm_get_populations(c, buf.data()) : mlbm_get_fields(c, buf.data()));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return set_error(MLBM_E_IO, std::string("save: cannot open ") + path);
+    const char magic[8] = {'M', 'L', 'B', 'M', 'S', 'T', '0', '1'};
+    int64_t hdr[4] = {c->n, c->K, c->params.model, c->steps};
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, 8, 4, f) == 4 &&
+              std::fwrite(&c->params, sizeof(mlbm_params), 1, f) == 1 &&
+              std::fwrite(buf.data(), 8, buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MLBM_OK : set_error(MLBM_E_IO, "save: write failed");
+}
+
+mlbm_status mlbm_load(mlbm_ctx* c, const char* path) {
+    if (!c || !path) return set_error(MLBM_E_INVALID, "load: NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return set_error(MLBM_E_IO, std::string("load: cannot open ") + path);
+    char magic[8];
+    int64_t hdr[4];
+    mlbm_params p;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MLBMST01", 8) == 0 &&
+              std::fread(hdr, 8, 4, f) == 4 && std::fread(&p, sizeof(p), 1, f) == 1;
+    if (!ok || hdr[0] != c->n || hdr[1] != c->K || hdr[2] != c->params.model) {
+        std::fclose(f);
+        return set_error(MLBM_E_IO, "load: file does not match this context");
+    }
+    const int per = c->params.model == MLBM_MODEL_BGK ? 9 : 3;
+    std::vector<double> buf((size_t)c->n * per);
+    ok = std::fread(buf.data(), 8, buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return set_error(MLBM_E_IO, "load: truncated file");
+    c->params = p;
+    set_collide(c);
+    if (per == 9) {
+        MLBM_TRY(upload(c, c->io, buf.data(), buf.size() * 8));
+        MLBM_CUDA(launch_set_bgk((int)c->n, c->perm, c->io, c->f8[c->cur], c->f0[c->cur], c->stream));
+    } else {
+        MLBM_TRY(upload(c, c->io, buf.data(), buf.size() * 8));
+        MLBM_CUDA(launch_set_tau1((int)c->n, c->perm, c->io, c->ruv[c->cur], c->stream));
+    }
+    MLBM_TRY(sync(c));
+    c->steps = hdr[3];
+    return MLBM_OK;
+}
+
+int64_t mlbm_reduce_scratch_doubles(int64_t n) { return n < 0 ? -1 : 6 * (int64_t)reduce_blocks(n); }
+
+mlbm_status mlbm_reduce_fields_device(const float* rho, const float* ux, const float* uy, const float* area,
+                                      const uint8_t* mask, int64_t n, double* scratch, int64_t scratch_len,
+                                      double* out, void* stream) {
+    clear_error();
+    if (!rho || !ux || !uy || !area || !scratch || !out || n < 0)
+        return set_error(MLBM_E_INVALID, "reduce_fields_device: NULL pointer or negative n");
+    if (scratch_len < mlbm_reduce_scratch_doubles(n))
+        return set_error(MLBM_E_INVALID, "reduce_fields_device: scratch too small");
+    MLBM_CUDA(launch_reduce_fields(rho, ux, uy, area, mask, n, scratch, out, static_cast<cudaStream_t>(stream)));
+    return MLBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,35 @@
+// Host-side launchers of the kernels in kernels.cu.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace mlbm {
+
+cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,
+                            float* f0out, const dev::Collide& C, int block, cudaStream_t st);
+cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C, int block,
+                             cudaStream_t st);
+cudaError_t launch_set_bgk(int n, const int* perm, const double* f, float4* f8, float* f0, cudaStream_t st);
+cudaError_t launch_get_bgk(int n, const int* perm, const float4* f8, const float* f0, double* f, cudaStream_t st);
+cudaError_t launch_set_bgk_equilibrium(int n, const int* perm, const double* ru, float4* f8, float* f0,
+                                       cudaStream_t st);
+cudaError_t launch_set_tau1(int n, const int* perm, const double* ru, float4* s, cudaStream_t st);
+cudaError_t launch_get_tau1(int n, const int* perm, const float4* s, double* ru, cudaStream_t st);
+cudaError_t launch_macroscopics(int model, int n, const int* perm, const float4* f8, const float* f0,
+                                const float4* ruv, float ax, float ay, float* rho, float* ux, float* uy, double* ru,
+                                cudaStream_t st);
+int force_blocks(int n_link_nodes);
+cudaError_t launch_force(const dev::Stencil& S, int model, int n_link_nodes, const int* link_nodes,
+                         const float* area_over_s2, const float4* f8, const float4* ruv, const dev::Collide& C,
+                         double* partial, double* out, cudaStream_t st);
+int reduce_blocks(int64_t n);
+cudaError_t launch_reduce_fields(const float* rho, const float* ux, const float* uy, const float* area,
+                                 const uint8_t* mask, int64_t n, double* partial, double* out, cudaStream_t st);
+cudaError_t launch_change(const float* ux, const float* uy, float* px, float* py, const uint8_t* mask, int64_t n,
+                          double* partial, double* out, cudaStream_t st);
+
+}  // namespace mlbm

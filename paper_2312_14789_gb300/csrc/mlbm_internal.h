@@ -1,0 +1,54 @@
+// Internal declarations shared by the library's translation units (host
+// stencil builder, CUDA step kernels, C-ABI glue).  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mlbm.h"
+
+namespace mlbm {
+
+// D2Q9 velocity set in the paper's order (Eq. (2)); weights (Eq. (8)).
+constexpr int kQ = 9;
+constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+constexpr int kOpp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+enum Kind : uint8_t { kKindWls = 0, kKindLagrange = 1, kKindEq = 2 };
+
+// Host-side result of mlbm_build_stencils, already in the Hilbert order the
+// device uses ("position" p = 0..n-1); perm[p] is the caller's node id.
+struct HostStencils {
+    int64_t n = 0;
+    int K = 0;
+    double s = 1.0;
+    int bb_mode = 0;
+    double box_area = 0.0;
+    std::vector<int64_t> perm;     // position -> caller id
+    std::vector<int64_t> inv;      // caller id -> position
+    std::vector<int32_t> idx;      // [n][K] neighbour positions, search order
+    std::vector<double> M;         // [n][6][K] least-squares matrix, units of s
+    std::vector<uint8_t> kind;     // Kind
+    std::vector<uint8_t> center;   // Lagrange block centre direction m
+    std::vector<double> lag_h;     // Lagrange block spacing
+    std::vector<int8_t> lag_slot;  // [n][9] stencil slot of block point (a, b)
+    std::vector<uint16_t> link_mask;
+    std::vector<double> q;         // [n][9]
+    std::vector<double> eqv;       // [n][3] rho_b, ux_b, uy_b
+    std::vector<double> area;      // [n]
+    mlbm_stencil_info info{};
+};
+
+}  // namespace mlbm
+
+struct mlbm_stencils {
+    mlbm::HostStencils h;
+};
+
+// error reporting shared by all translation units
+namespace mlbm {
+mlbm_status set_error(mlbm_status st, const std::string& msg);
+void clear_error();
+}  // namespace mlbm

@@ -1,0 +1,540 @@
+// Host (FP64) stencil builder behind mlbm_build_stencils.
+//
+// Per node, once per node set and streaming distance s (the paper's weight
+// precomputation, Sec. 2.2):
+//   1. K nearest nodes by a ring search over a uniform cell grid (periodic
+//      sides wrap; the minimum image of every offset is used, Sec. 3.2);
+//   2. the quadratic weighted least-squares matrix by Householder QR of
+//      sqrt(W) P (FP64), stored in units of s;
+//   3. the regular 3x3 block test for biquadratic Lagrange (Sec. 2.2);
+//   4. bounce-back links by intersecting the departure segment with the
+//      solids (Sec. 3.1, 3.2);
+//   5. a Hilbert-curve order of the nodes so that neighbour gathers on the
+//      GPU stay within a small window of memory.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "mlbm_internal.h"
+
+namespace mlbm {
+namespace {
+
+struct Box {
+    double x0, y0, x1, y1, lx, ly;
+    int side[4];
+    bool px, py;
+};
+
+inline double min_image(double d, double L, bool periodic) {
+    if (!periodic) return d;
+    if (d >= 0.5 * L) d -= L;
+    if (d < -0.5 * L) d += L;
+    return d;
+}
+
+// Uniform grid whose cells tile periodic extents exactly.
+struct CellGrid {
+    double x0 = 0, y0 = 0, cx = 1, cy = 1;
+    int ncx = 1, ncy = 1;
+    std::vector<int64_t> start, items;
+
+    int cell_x(double x) const {
+        int c = (int)std::floor((x - x0) / cx);
+        return c < 0 ? 0 : (c >= ncx ? ncx - 1 : c);
+    }
+    int cell_y(double y) const {
+        int c = (int)std::floor((y - y0) / cy);
+        return c < 0 ? 0 : (c >= ncy ? ncy - 1 : c);
+    }
+};
+
+CellGrid make_grid(const double* xy, int64_t n, const Box& b, int K) {
+    CellGrid g;
+    g.x0 = b.x0;
+    g.y0 = b.y0;
+    // about K/4 nodes per cell
+    double target = std::sqrt(b.lx * b.ly / (double)n * std::max(1, K / 4));
+    g.ncx = std::max(1, (int)std::floor(b.lx / target));
+    g.ncy = std::max(1, (int)std::floor(b.ly / target));
+    g.ncx = std::min(g.ncx, 1 << 15);
+    g.ncy = std::min(g.ncy, 1 << 15);
+    g.cx = b.lx / g.ncx;
+    g.cy = b.ly / g.ncy;
+    int64_t nc = (int64_t)g.ncx * g.ncy;
+    g.start.assign(nc + 1, 0);
+    std::vector<int64_t> cell(n);
+    for (int64_t i = 0; i < n; ++i) {
+        cell[i] = (int64_t)g.cell_y(xy[2 * i + 1]) * g.ncx + g.cell_x(xy[2 * i]);
+        g.start[cell[i] + 1]++;
+    }
+    for (int64_t c = 0; c < nc; ++c) g.start[c + 1] += g.start[c];
+    g.items.resize(n);
+    std::vector<int64_t> fill(g.start.begin(), g.start.end() - 1);
+    for (int64_t i = 0; i < n; ++i) g.items[fill[cell[i]]++] = i;  // ids ascending per cell
+    return g;
+}
+
+// K nearest of node i ordered by (d2, id), self included.
+void knn_one(const CellGrid& g, const double* xy, const Box& b, int64_t i, int K, int64_t* id, double* d2,
+             double* off) {
+    const double xi = xy[2 * i], yi = xy[2 * i + 1];
+    const int ci = g.cell_x(xi), cj = g.cell_y(yi);
+    int cnt = 0;
+    const int rmax = std::max(g.ncx, g.ncy) + 1;
+    const double cmin = std::min(g.cx, g.cy);
+    for (int r = 0; r <= rmax; ++r) {
+        for (int dy = -r; dy <= r; ++dy) {
+            int yy = cj + dy;
+            if (b.py) {
+                yy %= g.ncy;
+                if (yy < 0) yy += g.ncy;
+            } else if (yy < 0 || yy >= g.ncy) {
+                continue;
+            }
+            const bool edge_row = (dy == -r || dy == r);
+            for (int dx = -r; dx <= r; dx += (edge_row ? 1 : 2 * r)) {
+                int xx = ci + dx;
+                if (b.px) {
+                    xx %= g.ncx;
+                    if (xx < 0) xx += g.ncx;
+                } else if (xx < 0 || xx >= g.ncx) {
+                    if (r == 0) break;
+                    continue;
+                }
+                const int64_t c = (int64_t)yy * g.ncx + xx;
+                for (int64_t e = g.start[c]; e < g.start[c + 1]; ++e) {
+                    const int64_t j = g.items[e];
+                    const double ox = min_image(xy[2 * j] - xi, b.lx, b.px);
+                    const double oy = min_image(xy[2 * j + 1] - yi, b.ly, b.py);
+                    const double dd = ox * ox + oy * oy;
+                    if (cnt == K && (dd > d2[K - 1] || (dd == d2[K - 1] && j > id[K - 1]))) continue;
+                    bool dup = false;
+                    for (int m = 0; m < cnt; ++m)
+                        if (id[m] == j) { dup = true; break; }
+                    if (dup) continue;
+                    int pos = (cnt == K) ? K - 1 : cnt;
+                    while (pos > 0 && (d2[pos - 1] > dd || (d2[pos - 1] == dd && id[pos - 1] > j))) {
+                        d2[pos] = d2[pos - 1];
+                        id[pos] = id[pos - 1];
+                        off[2 * pos] = off[2 * pos - 2];
+                        off[2 * pos + 1] = off[2 * pos - 1];
+                        --pos;
+                    }
+                    d2[pos] = dd;
+                    id[pos] = j;
+                    off[2 * pos] = ox;
+                    off[2 * pos + 1] = oy;
+                    if (cnt < K) ++cnt;
+                }
+                if (r == 0) break;
+            }
+        }
+        // every unvisited node sits at least r cells away
+        if (cnt == K) {
+            const double reach = r * cmin;
+            if (d2[K - 1] < reach * reach) break;
+        }
+    }
+}
+
+// Quadratic WLS by Householder QR.  Returns 0, or 2 when cond(R)^2 > 1e12.
+int wls_qr(const double* off, int K, double s, double sigma_factor, double* M) {
+    double rK = 0;
+    for (int j = 0; j < K; ++j) rK = std::max(rK, std::sqrt(off[2 * j] * off[2 * j] + off[2 * j + 1] * off[2 * j + 1]));
+    if (!(rK > 0)) return 2;
+    const double sig2 = (sigma_factor * rK) * (sigma_factor * rK);
+    double A[32][6], sw[32];
+    for (int j = 0; j < K; ++j) {
+        const double x = off[2 * j], y = off[2 * j + 1];
+        sw[j] = std::sqrt(std::exp(-(x * x + y * y) / sig2));
+        const double u = x / rK, v = y / rK;
+        const double p[6] = {1.0, u, v, u * u, u * v, v * v};
+        for (int a = 0; a < 6; ++a) A[j][a] = sw[j] * p[a];
+    }
+    double V[6][32];  // Householder vectors
+    for (int c = 0; c < 6; ++c) {
+        double nrm = 0;
+        for (int j = c; j < K; ++j) nrm += A[j][c] * A[j][c];
+        nrm = std::sqrt(nrm);
+        if (nrm == 0) return 2;
+        const double alpha = A[c][c] > 0 ? -nrm : nrm;
+        double vv = 0;
+        for (int j = 0; j < K; ++j) V[c][j] = 0;
+        for (int j = c; j < K; ++j) V[c][j] = A[j][c];
+        V[c][c] -= alpha;
+        for (int j = c; j < K; ++j) vv += V[c][j] * V[c][j];
+        if (vv == 0) return 2;
+        for (int col = c; col < 6; ++col) {
+            double dot = 0;
+            for (int j = c; j < K; ++j) dot += V[c][j] * A[j][col];
+            const double f = 2.0 * dot / vv;
+            for (int j = c; j < K; ++j) A[j][col] -= f * V[c][j];
+        }
+        const double vn = std::sqrt(vv);
+        for (int j = c; j < K; ++j) V[c][j] /= vn;  // unit vector: H = I - 2 v v^T
+    }
+    // R = A[0:6][0:6] (upper), its inverse by back substitution
+    double Ri[6][6] = {};
+    for (int c = 0; c < 6; ++c) {
+        if (A[c][c] == 0) return 2;
+        Ri[c][c] = 1.0 / A[c][c];
+        for (int r = c - 1; r >= 0; --r) {
+            double acc = 0;
+            for (int m = r + 1; m <= c; ++m) acc += A[r][m] * Ri[m][c];
+            Ri[r][c] = -acc / A[r][r];
+        }
+    }
+    double nR = 0, nRi = 0;
+    for (int c = 0; c < 6; ++c) {
+        double a = 0, b = 0;
+        for (int r = 0; r <= c; ++r) { a += std::fabs(A[r][c]); b += std::fabs(Ri[r][c]); }
+        nR = std::max(nR, a);
+        nRi = std::max(nRi, b);
+    }
+    if ((nR * nRi) * (nR * nRi) > 1e12) return 2;
+    // Q1 = H_0 ... H_5 [I_6; 0]  (K x 6)
+    double Q[32][6];
+    for (int j = 0; j < K; ++j)
+        for (int a = 0; a < 6; ++a) Q[j][a] = (j == a) ? 1.0 : 0.0;
+    for (int c = 5; c >= 0; --c)
+        for (int col = 0; col < 6; ++col) {
+            double dot = 0;
+            for (int j = c; j < K; ++j) dot += V[c][j] * Q[j][col];
+            for (int j = c; j < K; ++j) Q[j][col] -= 2.0 * dot * V[c][j];
+        }
+    // M~ = R^-1 Q1^T diag(sqrt w), rows scaled by (s / rK)^deg
+    static const int deg[6] = {0, 1, 1, 2, 2, 2};
+    for (int a = 0; a < 6; ++a) {
+        const double sc = std::pow(s / rK, deg[a]);
+        for (int j = 0; j < K; ++j) {
+            double acc = 0;
+            for (int m = a; m < 6; ++m) acc += Ri[a][m] * Q[j][m];
+            M[a * K + j] = acc * sw[j] * sc;
+        }
+    }
+    return 0;
+}
+
+// Departure offsets and which directions interpolate (simple bounce-back
+// links copy the node's own population instead).
+void departures(double s, uint16_t mask, const double* q, int bb_mode, double* dx, double* dy, bool* use) {
+    use[0] = false;
+    for (int k = 1; k < 9; ++k) {
+        if (mask & (1u << k)) {
+            if (bb_mode == MLBM_BB_SIMPLE) {
+                use[k] = false;
+                dx[k] = dy[k] = 0;
+                continue;
+            }
+            const double t = 1.0 - 2.0 * q[k];
+            dx[k] = t * s * kEx[k];
+            dy[k] = t * s * kEy[k];
+        } else {
+            dx[k] = -s * kEx[k];
+            dy[k] = -s * kEy[k];
+        }
+        use[k] = true;
+    }
+}
+
+// Axis-aligned 3x3 block (spacing h = nearest non-zero offset) centred on
+// x + h e_m, m tried in D2Q9 order, containing every departure point.
+bool find_block(const double* off, int K, const double* dx, const double* dy, const bool* use, double tol,
+                int8_t* slot, double* h_out, uint8_t* center) {
+    double h = 0;
+    for (int j = 0; j < K; ++j) {
+        const double r = std::sqrt(off[2 * j] * off[2 * j] + off[2 * j + 1] * off[2 * j + 1]);
+        if (r > 0 && (h == 0 || r < h)) h = r;
+    }
+    if (h == 0) return false;
+    for (int m = 0; m < 9; ++m) {
+        const double cx = kEx[m] * h, cy = kEy[m] * h;
+        bool ok = true;
+        for (int k = 1; k < 9 && ok; ++k)
+            if (use[k] && (std::fabs(dx[k] - cx) > h * (1.0 + tol) || std::fabs(dy[k] - cy) > h * (1.0 + tol)))
+                ok = false;
+        int8_t sl[9];
+        for (int b = 0; b < 3 && ok; ++b)
+            for (int a = 0; a < 3 && ok; ++a) {
+                const double px = cx + (a - 1) * h, py = cy + (b - 1) * h;
+                int found = -1;
+                for (int j = 0; j < K; ++j)
+                    if (std::fabs(off[2 * j] - px) <= tol * h && std::fabs(off[2 * j + 1] - py) <= tol * h) {
+                        found = j;
+                        break;
+                    }
+                if (found < 0) ok = false;
+                else sl[b * 3 + a] = (int8_t)found;
+            }
+        if (ok) {
+            std::memcpy(slot, sl, 9);
+            *h_out = h;
+            *center = (uint8_t)m;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Bounce-back links of node (x, y).  Returns 0, or 8 when the node is inside
+// a solid.
+int links_of(double x, double y, double s, const Box& b, const double* disks, int nd, uint16_t* mask, double* q) {
+    const double tol = 1e-9 * s;
+    *mask = 0;
+    for (int k = 0; k < 9; ++k) q[k] = 0;
+    for (int k = 1; k < 9; ++k) {
+        const double vx = -s * kEx[k], vy = -s * kEy[k];
+        double best = 2.0;
+        auto side_hit = [&](double dist, double speed) -> int {
+            // dist: distance from the node to the wall along the inward normal,
+            // speed > 0: approach rate per unit t
+            if (dist < -tol) return 8;
+            const double t = dist <= tol ? 0.0 : dist / speed;
+            if (t < 1.0 && t < best) best = t;
+            return 0;
+        };
+        if (b.side[2] == MLBM_SIDE_SOLID && vy < 0 && side_hit(y - b.y0, -vy)) return 8;
+        if (b.side[3] == MLBM_SIDE_SOLID && vy > 0 && side_hit(b.y1 - y, vy)) return 8;
+        if (b.side[0] == MLBM_SIDE_SOLID && vx < 0 && side_hit(x - b.x0, -vx)) return 8;
+        if (b.side[1] == MLBM_SIDE_SOLID && vx > 0 && side_hit(b.x1 - x, vx)) return 8;
+        for (int d = 0; d < nd; ++d) {
+            for (int ix = -1; ix <= 1; ++ix) {
+                if (ix != 0 && !b.px) continue;
+                for (int iy = -1; iy <= 1; ++iy) {
+                    if (iy != 0 && !b.py) continue;
+                    const double cxd = disks[3 * d] + ix * b.lx, cyd = disks[3 * d + 1] + iy * b.ly;
+                    const double R = disks[3 * d + 2];
+                    const double rx = x - cxd, ry = y - cyd;
+                    const double dist = std::sqrt(rx * rx + ry * ry);
+                    if (dist < R * (1.0 - 1e-9)) return 8;
+                    const double bb = rx * vx + ry * vy;
+                    if (dist <= R * (1.0 + 1e-9)) {
+                        if (bb < 0) best = 0.0;
+                        continue;
+                    }
+                    const double aa = vx * vx + vy * vy;
+                    const double cc = rx * rx + ry * ry - R * R;
+                    const double disc = bb * bb - aa * cc;
+                    if (disc <= 0) continue;
+                    const double t = (-bb - std::sqrt(disc)) / aa;
+                    if (t >= 0 && t < 1.0 && t < best) best = t;
+                }
+            }
+        }
+        if (best < 1.0) {
+            *mask |= (uint16_t)(1u << k);
+            q[k] = best;
+        }
+    }
+    return 0;
+}
+
+// Hilbert index of (x, y) in [0, 2^order)^2.
+uint64_t hilbert_index(uint32_t x, uint32_t y, int order) {
+    uint64_t d = 0;
+    for (uint32_t sq = 1u << (order - 1); sq > 0; sq >>= 1) {
+        const uint32_t rx = (x & sq) ? 1 : 0;
+        const uint32_t ry = (y & sq) ? 1 : 0;
+        d += (uint64_t)sq * sq * ((3 * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = sq - 1 - x;
+                y = sq - 1 - y;
+            }
+            std::swap(x, y);
+        }
+    }
+    return d;
+}
+
+}  // namespace
+}  // namespace mlbm
+
+using namespace mlbm;
+
+extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
+                                           double sigma_factor, int bb_mode, int use_lagrange,
+                                           mlbm_stencils** out) {
+    clear_error();
+    if (!out) return set_error(MLBM_E_INVALID, "build_stencils: out is NULL");
+    *out = nullptr;
+    if (!nodes || !geo || !nodes->xy || !nodes->node_class)
+        return set_error(MLBM_E_INVALID, "build_stencils: nodes, geometry, xy and node_class are required");
+    const int64_t n = nodes->n;
+    if (n < 1 || n > (int64_t(1) << 31) - 1) return set_error(MLBM_E_INVALID, "build_stencils: bad node count");
+    if (K < 6 || K > 32 || K % 4 != 0 || K > n)
+        return set_error(MLBM_E_INVALID, "build_stencils: K must be a multiple of 4 in [8, 32] and <= n");
+    if (use_lagrange && K < 9) return set_error(MLBM_E_INVALID, "build_stencils: Lagrange needs K >= 9");
+    if (!(s > 0) || !(sigma_factor > 0)) return set_error(MLBM_E_INVALID, "build_stencils: s and sigma must be > 0");
+    if (bb_mode != MLBM_BB_SIMPLE && bb_mode != MLBM_BB_INTERPOLATED)
+        return set_error(MLBM_E_INVALID, "build_stencils: bad bb_mode");
+    Box b;
+    b.x0 = geo->x0; b.y0 = geo->y0; b.x1 = geo->x1; b.y1 = geo->y1;
+    b.lx = b.x1 - b.x0; b.ly = b.y1 - b.y0;
+    for (int i = 0; i < 4; ++i) {
+        b.side[i] = geo->side[i];
+        if (b.side[i] < 0 || b.side[i] > 2) return set_error(MLBM_E_INVALID, "build_stencils: bad side type");
+    }
+    if (!(b.lx > 0) || !(b.ly > 0)) return set_error(MLBM_E_INVALID, "build_stencils: empty box");
+    if ((b.side[0] == MLBM_SIDE_PERIODIC) != (b.side[1] == MLBM_SIDE_PERIODIC) ||
+        (b.side[2] == MLBM_SIDE_PERIODIC) != (b.side[3] == MLBM_SIDE_PERIODIC))
+        return set_error(MLBM_E_INVALID, "build_stencils: periodic sides must come in pairs");
+    b.px = b.side[0] == MLBM_SIDE_PERIODIC;
+    b.py = b.side[2] == MLBM_SIDE_PERIODIC;
+    if (geo->n_disks < 0 || (geo->n_disks > 0 && !geo->disks))
+        return set_error(MLBM_E_INVALID, "build_stencils: bad disks");
+    for (int64_t i = 0; i < n; ++i) {
+        if (nodes->node_class[i] > MLBM_NODE_EQ) return set_error(MLBM_E_INVALID, "build_stencils: bad node class");
+        if (nodes->node_class[i] == MLBM_NODE_EQ && !nodes->eq_values)
+            return set_error(MLBM_E_INVALID, "build_stencils: equilibrium nodes need eq_values");
+        if (!std::isfinite(nodes->xy[2 * i]) || !std::isfinite(nodes->xy[2 * i + 1]))
+            return set_error(MLBM_E_INVALID, "build_stencils: non-finite coordinate");
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    auto* st = new (std::nothrow) mlbm_stencils;
+    if (!st) return set_error(MLBM_E_OOM, "build_stencils: out of host memory");
+    HostStencils& H = st->h;
+    H.n = n;
+    H.K = K;
+    H.s = s;
+    H.bb_mode = bb_mode;
+    H.box_area = b.lx * b.ly;
+    const double* xy = nodes->xy;
+    const CellGrid grid = make_grid(xy, n, b, K);
+
+    // caller-order work arrays
+    std::vector<int64_t> nid((size_t)n * K);
+    std::vector<double> off((size_t)n * K * 2);
+    std::vector<double> Mc((size_t)n * 6 * K, 0.0);
+    std::vector<uint8_t> kind(n), center(n, 0);
+    std::vector<double> lagh(n, 0.0), qc((size_t)n * 9, 0.0);
+    std::vector<int8_t> slot((size_t)n * 9, 0);
+    std::vector<uint16_t> mask(n, 0);
+    int64_t bad_node = -1;
+    int bad_code = 0;
+#pragma omp parallel
+    {
+        std::vector<double> d2(K);
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            knn_one(grid, xy, b, i, K, &nid[(size_t)i * K], d2.data(), &off[(size_t)i * K * 2]);
+            if (nodes->node_class[i] == MLBM_NODE_EQ) {
+                kind[i] = kKindEq;
+                continue;
+            }
+            int code = links_of(xy[2 * i], xy[2 * i + 1], s, b, geo->disks, geo->n_disks, &mask[i], &qc[(size_t)i * 9]);
+            if (code) {
+#pragma omp critical
+                { if (bad_node < 0 || i < bad_node) { bad_node = i; bad_code = code; } }
+                continue;
+            }
+            double dx[9], dy[9];
+            bool use[9];
+            departures(s, mask[i], &qc[(size_t)i * 9], bb_mode, dx, dy, use);
+            if (use_lagrange && find_block(&off[(size_t)i * K * 2], K, dx, dy, use, 1e-9, &slot[(size_t)i * 9],
+                                           &lagh[i], &center[i])) {
+                kind[i] = kKindLagrange;
+                continue;
+            }
+            kind[i] = kKindWls;
+            code = wls_qr(&off[(size_t)i * K * 2], K, s, sigma_factor, &Mc[(size_t)i * 6 * K]);
+            if (code) {
+#pragma omp critical
+                { if (bad_node < 0 || i < bad_node) { bad_node = i; bad_code = code; } }
+            }
+        }
+    }
+    if (bad_node >= 0) {
+        delete st;
+        if (bad_code == 8)
+            return set_error(MLBM_E_GEOMETRY, "build_stencils: node " + std::to_string(bad_node) + " lies inside a solid");
+        return set_error(MLBM_E_SINGULAR_STENCIL,
+                         "build_stencils: degenerate least-squares stencil at node " + std::to_string(bad_node));
+    }
+
+    // Hilbert order
+    std::vector<uint64_t> key(n);
+    const int order = 16;
+    const double scale = (double)((1u << order) - 1);
+    for (int64_t i = 0; i < n; ++i) {
+        double u = (xy[2 * i] - b.x0) / b.lx, v = (xy[2 * i + 1] - b.y0) / b.ly;
+        u = std::min(1.0, std::max(0.0, u));
+        v = std::min(1.0, std::max(0.0, v));
+        key[i] = hilbert_index((uint32_t)(u * scale), (uint32_t)(v * scale), order);
+    }
+    H.perm.resize(n);
+    std::iota(H.perm.begin(), H.perm.end(), 0);
+    std::stable_sort(H.perm.begin(), H.perm.end(), [&](int64_t a, int64_t c) { return key[a] < key[c]; });
+    H.inv.resize(n);
+    for (int64_t p = 0; p < n; ++p) H.inv[H.perm[p]] = p;
+
+    H.idx.resize((size_t)n * K);
+    H.M.assign((size_t)n * 6 * K, 0.0);
+    H.kind.resize(n);
+    H.center.resize(n);
+    H.lag_h.resize(n);
+    H.lag_slot.resize((size_t)n * 9);
+    H.link_mask.resize(n);
+    H.q.resize((size_t)n * 9);
+    H.eqv.assign((size_t)n * 3, 0.0);
+    H.area.resize(n);
+    mlbm_stencil_info& I = H.info;
+    I = mlbm_stencil_info{};
+    I.n = n;
+    I.K = K;
+    I.s = s;
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t i = H.perm[p];
+        for (int j = 0; j < K; ++j) H.idx[(size_t)p * K + j] = (int32_t)H.inv[nid[(size_t)i * K + j]];
+        std::memcpy(&H.M[(size_t)p * 6 * K], &Mc[(size_t)i * 6 * K], sizeof(double) * 6 * K);
+        H.kind[p] = kind[i];
+        H.center[p] = center[i];
+        H.lag_h[p] = lagh[i];
+        std::memcpy(&H.lag_slot[(size_t)p * 9], &slot[(size_t)i * 9], 9);
+        H.link_mask[p] = mask[i];
+        std::memcpy(&H.q[(size_t)p * 9], &qc[(size_t)i * 9], sizeof(double) * 9);
+        if (kind[i] == kKindEq)
+            for (int c = 0; c < 3; ++c) H.eqv[(size_t)p * 3 + c] = nodes->eq_values[(size_t)i * 3 + c];
+        H.area[p] = nodes->area ? nodes->area[i] : 1.0;
+        if (kind[i] == kKindWls) I.n_wls++;
+        else if (kind[i] == kKindLagrange) I.n_lagrange++;
+        else I.n_eq++;
+        if (mask[i]) {
+            I.n_link_nodes++;
+            for (int k = 1; k < 9; ++k) I.n_links += (mask[i] >> k) & 1;
+        }
+    }
+    I.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = st;
+    return MLBM_OK;
+}
+
+extern "C" void mlbm_stencils_free(mlbm_stencils* st) { delete st; }
+
+extern "C" mlbm_status mlbm_stencils_info(const mlbm_stencils* st, mlbm_stencil_info* info) {
+    if (!st || !info) return set_error(MLBM_E_INVALID, "stencils_info: NULL argument");
+    *info = st->h.info;
+    return MLBM_OK;
+}
+
+extern "C" mlbm_status mlbm_stencils_export(const mlbm_stencils* st, int64_t* idx, double* M, int32_t* kind,
+                                            int32_t* link_mask, double* q, double* lag_h, int32_t* lag_center) {
+    if (!st) return set_error(MLBM_E_INVALID, "stencils_export: NULL stencils");
+    const HostStencils& H = st->h;
+    const int K = H.K;
+    for (int64_t p = 0; p < H.n; ++p) {
+        const int64_t i = H.perm[p];
+        if (idx)
+            for (int j = 0; j < K; ++j) idx[(size_t)i * K + j] = H.perm[H.idx[(size_t)p * K + j]];
+        if (M) std::memcpy(&M[(size_t)i * 6 * K], &H.M[(size_t)p * 6 * K], sizeof(double) * 6 * K);
+        if (kind) kind[i] = H.kind[p];
+        if (link_mask) link_mask[i] = H.link_mask[p];
+        if (q) std::memcpy(&q[(size_t)i * 9], &H.q[(size_t)p * 9], sizeof(double) * 9);
+        if (lag_h) lag_h[i] = H.lag_h[p];
+        if (lag_center) lag_center[i] = H.center[p];
+    }
+    return MLBM_OK;
+}

@@ -33,8 +33,8 @@ typedef struct {
     const double* rgrid; int nrx, nry;
     const double* disks; int ndisks; double clear_frac;
     /* coarse bucket grid over disks: dcell_start[c]..dcell_start[c+1] index dcell_list */
-    double dcell; int dncx, dncy; int* dcell_start; int* dcell_list;
-    double cell; int ncx, ncy;
+    double dcellx, dcelly; int dncx, dncy; int* dcell_start; int* dcell_list;
+    double cell, cellx, celly; int ncx, ncy;
     int64_t* head; int64_t* next;
     double* pts; int64_t npts, cap;
     double rmax;
@@ -63,7 +63,7 @@ static double wrapd(double d, double L, int per) {
 }
 
 static int cell_of(const pd_t* p, double x, double y, int* cx, int* cy) {
-    int ix = (int)floor((x - p->x0) / p->cell), iy = (int)floor((y - p->y0) / p->cell);
+    int ix = (int)floor((x - p->x0) / p->cellx), iy = (int)floor((y - p->y0) / p->celly);
     if (ix < 0) ix = 0; if (iy < 0) iy = 0;
     if (ix >= p->ncx) ix = p->ncx - 1; if (iy >= p->ncy) iy = p->ncy - 1;
     *cx = ix; *cy = iy;
@@ -85,13 +85,13 @@ static int add_point(pd_t* p, double x, double y) {
 static int far_from_points(const pd_t* p, double x, double y, double r) {
     int cx, cy;
     cell_of(p, x, y, &cx, &cy);
-    int reach = (int)ceil(r / p->cell) + 1;
+    int reachx = (int)ceil(r / p->cellx) + 1, reachy = (int)ceil(r / p->celly) + 1;
     double r2 = r * r;
-    for (int dy = -reach; dy <= reach; ++dy) {
+    for (int dy = -reachy; dy <= reachy; ++dy) {
         int yy = cy + dy;
         if (p->py) { yy %= p->ncy; if (yy < 0) yy += p->ncy; }
         else if (yy < 0 || yy >= p->ncy) continue;
-        for (int dx = -reach; dx <= reach; ++dx) {
+        for (int dx = -reachx; dx <= reachx; ++dx) {
             int xx = cx + dx;
             if (p->px) { xx %= p->ncx; if (xx < 0) xx += p->ncx; }
             else if (xx < 0 || xx >= p->ncx) continue;
@@ -107,7 +107,7 @@ static int far_from_points(const pd_t* p, double x, double y, double r) {
 
 static int outside_disks(const pd_t* p, double x, double y, double clear) {
     if (p->ndisks == 0) return 1;
-    int ix = (int)floor((x - p->x0) / p->dcell), iy = (int)floor((y - p->y0) / p->dcell);
+    int ix = (int)floor((x - p->x0) / p->dcellx), iy = (int)floor((y - p->y0) / p->dcelly);
     if (ix < 0) ix = 0; if (iy < 0) iy = 0;
     if (ix >= p->dncx) ix = p->dncx - 1; if (iy >= p->dncy) iy = p->dncy - 1;
     int c = iy * p->dncx + ix;
@@ -151,10 +151,12 @@ int64_t pd_sample(double x0, double y0, double x1, double y1, int periodic_x, in
     {
         double dmax = 0;
         for (int i = 0; i < ndisks; ++i) if (disks[3 * i + 2] > dmax) dmax = disks[3 * i + 2];
-        p.dcell = dmax + 2 * rmax + 1e-9;
-        if (p.dcell <= 0) p.dcell = 1;
-        p.dncx = (int)ceil(p.lx / p.dcell); p.dncy = (int)ceil(p.ly / p.dcell);
+        /* cells at least dmin wide that tile each side exactly, so periodic
+           wrapping by cell index matches the geometry */
+        double dmin = dmax + 2 * rmax + 1e-9;
+        p.dncx = (int)floor(p.lx / dmin); p.dncy = (int)floor(p.ly / dmin);
         if (p.dncx < 1) p.dncx = 1; if (p.dncy < 1) p.dncy = 1;
+        p.dcellx = p.lx / p.dncx; p.dcelly = p.ly / p.dncy;
         int nc = p.dncx * p.dncy;
         p.dcell_start = (int*)calloc(nc + 1, sizeof(int));
         int* cnt = (int*)calloc(nc, sizeof(int));
@@ -167,8 +169,8 @@ int64_t pd_sample(double x0, double y0, double x1, double y1, int periodic_x, in
             }
             for (int i = 0; i < ndisks; ++i) {
                 double cx = disks[3 * i], cy = disks[3 * i + 1], reach = disks[3 * i + 2] + 2 * rmax;
-                int ax = (int)floor((cx - reach - x0) / p.dcell), bx = (int)floor((cx + reach - x0) / p.dcell);
-                int ay = (int)floor((cy - reach - y0) / p.dcell), by = (int)floor((cy + reach - y0) / p.dcell);
+                int ax = (int)floor((cx - reach - x0) / p.dcellx), bx = (int)floor((cx + reach - x0) / p.dcellx);
+                int ay = (int)floor((cy - reach - y0) / p.dcelly), by = (int)floor((cy + reach - y0) / p.dcelly);
                 for (int yy = ay; yy <= by; ++yy) {
                     int wy = yy;
                     if (p.py) { wy %= p.dncy; if (wy < 0) wy += p.dncy; }
@@ -207,6 +209,7 @@ int64_t pd_sample(double x0, double y0, double x1, double y1, int periodic_x, in
     p.cell = rmin / sqrt(2.0);
     p.ncx = (int)ceil(p.lx / p.cell); p.ncy = (int)ceil(p.ly / p.cell);
     if (p.ncx < 1) p.ncx = 1; if (p.ncy < 1) p.ncy = 1;
+    p.cellx = p.lx / p.ncx; p.celly = p.ly / p.ncy;
     int64_t ncell = (int64_t)p.ncx * p.ncy;
     p.head = (int64_t*)malloc(sizeof(int64_t) * ncell);
     p.next = (int64_t*)malloc(sizeof(int64_t) * max_out);

@@ -1,0 +1,293 @@
+"""Thin ctypes binding of the C ABI in include/mlbm.h (argument marshalling only).
+
+Every function here forwards to libmlbm.so with the same name; all compute
+happens in the library (host stencil builder, CUDA kernels).  There is no
+Python fallback: if the library cannot be built or loaded, importing fails
+with the reason.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+MODEL_BGK, MODEL_TAU1 = 0, 1
+BB_SIMPLE, BB_INTERPOLATED = 0, 1
+NODE_FLUID, NODE_WALL, NODE_EQ = 0, 1, 2
+SIDE_PERIODIC, SIDE_SOLID, SIDE_OPEN = 0, 1, 2
+
+STATUS = {0: "OK", 1: "INVALID", 2: "SINGULAR_STENCIL", 3: "CUDA", 4: "OOM", 5: "DIVERGED", 6: "TIMEOUT",
+          7: "NOT_CONVERGED", 8: "GEOMETRY", 9: "IO"}
+
+_i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+class MlbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mlbm {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Nodes(ctypes.Structure):
+    _fields_ = [("n", _i64), ("xy", _vp), ("node_class", _vp), ("eq_values", _vp), ("area", _vp)]
+
+
+class _Geometry(ctypes.Structure):
+    _fields_ = [("x0", _dbl), ("y0", _dbl), ("x1", _dbl), ("y1", _dbl), ("side", _i32 * 4),
+                ("n_disks", _i32), ("disks", _vp)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("model", _i32), ("tau", _dbl), ("tau_minus", _dbl), ("gx", _dbl), ("gy", _dbl)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", _i64), ("K", _i32), ("s", _dbl), ("n_wls", _i64), ("n_lagrange", _i64), ("n_eq", _i64),
+                ("n_link_nodes", _i64), ("n_links", _i64), ("build_seconds", _dbl)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def lib():
+    """Build (if stale) and load libmlbm.so.  Raises when either fails."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            L = ctypes.CDLL(_build.build())
+            st = ctypes.c_int
+            sig = {
+                "mlbm_build_stencils": (st, [_vp, _vp, _i32, _dbl, _dbl, _i32, _i32, _vp]),
+                "mlbm_stencils_free": (None, [_vp]),
+                "mlbm_stencils_info": (st, [_vp, _vp]),
+                "mlbm_stencils_export": (st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+                "mlbm_init": (st, [_vp, _vp, _vp, _vp, _vp]),
+                "mlbm_destroy": (None, [_vp]),
+                "mlbm_set_stream": (st, [_vp, _vp]),
+                "mlbm_set_populations": (st, [_vp, _vp]),
+                "mlbm_set_fields": (st, [_vp, _vp]),
+                "mlbm_get_populations": (st, [_vp, _vp]),
+                "mlbm_get_fields": (st, [_vp, _vp]),
+                "mlbm_step": (st, [_vp, _i64]),
+                "mlbm_step_count": (_i64, [_vp]),
+                "mlbm_macroscopics": (st, [_vp, _vp, _vp]),
+                "mlbm_drag_lift": (st, [_vp, _dbl, _dbl, _vp, _vp, _vp, _vp]),
+                "mlbm_permeability": (st, [_vp, _vp, _vp, _vp, _vp]),
+                "mlbm_run_to_steady": (st, [_vp, _dbl, _i64, _i64, _vp]),
+                "mlbm_save": (st, [_vp, ctypes.c_char_p]),
+                "mlbm_load": (st, [_vp, ctypes.c_char_p]),
+                "mlbm_set_timing": (st, [_vp, _i32]),
+                "mlbm_last_step_ms": (_dbl, [_vp]),
+                "mlbm_reduce_scratch_doubles": (_i64, [_i64]),
+                "mlbm_reduce_fields_device": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
+                "mlbm_last_error": (ctypes.c_char_p, []),
+                "mlbm_version": (ctypes.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _check(status):
+    if status != 0:
+        raise MlbmError(status, lib().mlbm_last_error().decode())
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def version() -> str:
+    return lib().mlbm_version().decode()
+
+
+# ------------------------------------------------------------------ stencils
+class Stencils:
+    def __init__(self, handle, n, K, keep):
+        self.handle, self.n, self.K = handle, n, K
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.mlbm_stencils_free(self.handle)
+            self.handle = None
+
+
+def build_stencils(xy, node_class, box, sides, disks=None, eq_values=None, area=None, K=16, s=1.0,
+                   sigma_factor=0.7071067811865476, bb_mode=BB_INTERPOLATED, use_lagrange=True) -> Stencils:
+    xy = _f64(xy)
+    n = xy.shape[0]
+    cls = np.ascontiguousarray(node_class, dtype=np.uint8)
+    eqv = _f64(eq_values)
+    ar = _f64(area)
+    dk = _f64(np.zeros((0, 3)) if disks is None else np.asarray(disks).reshape(-1, 3))
+    nodes = _Nodes(n, _ptr(xy), _ptr(cls), _ptr(eqv), _ptr(ar))
+    geo = _Geometry(float(box[0]), float(box[1]), float(box[2]), float(box[3]), (_i32 * 4)(*[int(v) for v in sides]),
+                    len(dk), _ptr(dk) if len(dk) else None)
+    h = _vp()
+    _check(lib().mlbm_build_stencils(ctypes.byref(nodes), ctypes.byref(geo), int(K), float(s), float(sigma_factor),
+                                     int(bb_mode), int(bool(use_lagrange)), ctypes.byref(h)))
+    return Stencils(h, n, int(K), None)
+
+
+def build_stencils_for(w, **kw) -> Stencils:
+    """build_stencils for an inputs.Workload."""
+    return build_stencils(w.xy, w.node_class, w.box, w.sides, w.disks, w.eq_values, w.area, **kw)
+
+
+def stencils_info(st: Stencils) -> dict:
+    info = _Info()
+    _check(lib().mlbm_stencils_info(st.handle, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in _Info._fields_}
+
+
+def stencils_export(st: Stencils) -> dict:
+    n, K = st.n, st.K
+    out = {"idx": np.empty((n, K), np.int64), "M": np.empty((n, 6, K)), "kind": np.empty(n, np.int32),
+           "link_mask": np.empty(n, np.int32), "q": np.empty((n, 9)), "lag_h": np.empty(n),
+           "lag_center": np.empty(n, np.int32)}
+    _check(lib().mlbm_stencils_export(st.handle, *[_ptr(out[k]) for k in
+                                                   ("idx", "M", "kind", "link_mask", "q", "lag_h", "lag_center")]))
+    return out
+
+
+# ------------------------------------------------------------------- context
+@dataclass
+class Params:
+    model: int = MODEL_BGK
+    tau: float = 0.8
+    tau_minus: float = 0.0
+    gx: float = 0.0
+    gy: float = 0.0
+
+
+class Context:
+    def __init__(self, handle, n, model, stencils):
+        self.handle, self.n, self.model = handle, n, model
+        self._stencils = stencils
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.mlbm_destroy(self.handle)
+            self.handle = None
+
+
+def init(st: Stencils, params: Params, rho0=None, u0=None) -> Context:
+    p = _Params(int(params.model), float(params.tau), float(params.tau_minus), float(params.gx), float(params.gy))
+    r = _f64(rho0)
+    u = _f64(u0)
+    h = _vp()
+    _check(lib().mlbm_init(ctypes.byref(h), st.handle, ctypes.byref(p), _ptr(r), _ptr(u)))
+    return Context(h, st.n, params.model, st)
+
+
+def destroy(ctx: Context):
+    if ctx.handle:
+        lib().mlbm_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def set_stream(ctx: Context, stream_handle: int | None):
+    _check(lib().mlbm_set_stream(ctx.handle, _vp(stream_handle) if stream_handle else None))
+
+
+def set_populations(ctx: Context, f):
+    f = _f64(f)
+    assert f.shape == (ctx.n, 9)
+    _check(lib().mlbm_set_populations(ctx.handle, _ptr(f)))
+
+
+def set_fields(ctx: Context, rho_u):
+    a = _f64(rho_u)
+    assert a.shape == (ctx.n, 3)
+    _check(lib().mlbm_set_fields(ctx.handle, _ptr(a)))
+
+
+def get_populations(ctx: Context) -> np.ndarray:
+    f = np.empty((ctx.n, 9))
+    _check(lib().mlbm_get_populations(ctx.handle, _ptr(f)))
+    return f
+
+
+def get_fields(ctx: Context) -> np.ndarray:
+    a = np.empty((ctx.n, 3))
+    _check(lib().mlbm_get_fields(ctx.handle, _ptr(a)))
+    return a
+
+
+def step(ctx: Context, n_steps: int = 1):
+    _check(lib().mlbm_step(ctx.handle, int(n_steps)))
+
+
+def step_count(ctx: Context) -> int:
+    return int(lib().mlbm_step_count(ctx.handle))
+
+
+def macroscopics(ctx: Context):
+    rho = np.empty(ctx.n)
+    u = np.empty((ctx.n, 2))
+    _check(lib().mlbm_macroscopics(ctx.handle, _ptr(rho), _ptr(u)))
+    return rho, u
+
+
+def drag_lift(ctx: Context, ref_length: float = 1.0, u_ref: float = 1.0):
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(lib().mlbm_drag_lift(ctx.handle, float(ref_length), float(u_ref), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def permeability(ctx: Context):
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(lib().mlbm_permeability(ctx.handle, *[ctypes.byref(x) for x in v]))
+    k, us, ui, tv = (x.value for x in v)
+    return {"k": k, "u_superficial": us, "u_intrinsic": ui, "tortuosity": tv}
+
+
+def run_to_steady(ctx: Context, tol: float, window: int, max_steps: int, raise_on_max: bool = True) -> int:
+    taken = ctypes.c_int64()
+    st = lib().mlbm_run_to_steady(ctx.handle, float(tol), int(window), int(max_steps), ctypes.byref(taken))
+    if st == 7 and not raise_on_max:
+        return -int(taken.value)
+    _check(st)
+    return int(taken.value)
+
+
+def save(ctx: Context, path: str):
+    _check(lib().mlbm_save(ctx.handle, path.encode()))
+
+
+def load(ctx: Context, path: str):
+    _check(lib().mlbm_load(ctx.handle, path.encode()))
+
+
+def set_timing(ctx: Context, enable: bool):
+    _check(lib().mlbm_set_timing(ctx.handle, int(bool(enable))))
+
+
+def last_step_ms(ctx: Context) -> float:
+    return float(lib().mlbm_last_step_ms(ctx.handle))
+
+
+def reduce_scratch_doubles(n: int) -> int:
+    return int(lib().mlbm_reduce_scratch_doubles(int(n)))
+
+
+def reduce_fields_device(rho_ptr, ux_ptr, uy_ptr, area_ptr, mask_ptr, n, scratch_ptr, scratch_len, out_ptr,
+                         stream_handle=None):
+    """Device pointers (ints), e.g. torch tensor .data_ptr() values."""
+    _check(lib().mlbm_reduce_fields_device(_vp(rho_ptr), _vp(ux_ptr), _vp(uy_ptr), _vp(area_ptr),
+                                           _vp(mask_ptr) if mask_ptr else None, int(n), _vp(scratch_ptr),
+                                           int(scratch_len), _vp(out_ptr),
+                                           _vp(stream_handle) if stream_handle else None))

@@ -1,0 +1,44 @@
+"""Run the fused step on a named workload for a few steps (for profilers).
+
+    python -m paper_2312_14789_gb300.profile_step --workload karman --steps 3
+    python -m paper_2312_14789_gb300.profile_step --workload porous --steps 3
+
+karman: the ~260k-node cylinder channel, BGK, K = 16 (the benchmark case);
+porous: the ~1M-node porous box, tau = 1, K = 16, s = 1/2.
+No timing is reported; the process exits 0 when the steps ran.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_2312_14789_gb300 import inputs as I  # noqa: E402
+from paper_2312_14789_gb300 import mlbm  # noqa: E402
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="karman", choices=["karman", "porous"])
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--n-target", type=int, default=1_000_000)
+    args = ap.parse_args()
+    if args.workload == "karman":
+        w = I.karman(seed=2)
+        st = mlbm.build_stencils_for(w, K=16, s=1.0, bb_mode=mlbm.BB_SIMPLE)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, 0.56, 0.0, 0.0, 0.0))
+    else:
+        w = I.porous(seed=3, n_target=args.n_target)
+        st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=mlbm.BB_INTERPOLATED)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, 1e-6, 0.0))
+    mlbm.step(ctx, args.warmup + args.steps)
+    rho, _ = mlbm.macroscopics(ctx)
+    print(f"{args.workload}: {w.n} nodes, {args.warmup + args.steps} steps, mean rho {rho.mean():.6f}")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,101 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+* libmlbm.so loads and exports every function include/mlbm.h declares.
+* The host stencil builder (grid neighbour search, Householder QR, block
+  detection, link geometry) agrees with the oracle on the same node sets:
+  neighbour ids and order bit-exact, node kinds / links exact, q and the
+  least-squares matrix to FP64 round-off.
+* Argument and geometry errors come back as status codes.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_14789_gb300 import inputs as I
+from paper_2312_14789_gb300 import mlbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "mlbm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mlbm_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = mlbm.lib()
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    assert "sm_103a" in mlbm.version()
+
+
+def _compare(w, K, s, bb_mode, use_lagrange=True, sigma=0.7071067811865476):
+    st = mlbm.build_stencils_for(w, K=K, s=s, sigma_factor=sigma, bb_mode=bb_mode, use_lagrange=use_lagrange)
+    ex = mlbm.stencils_export(st)
+    op = O.Operator(w, K=K, s=s, sigma_factor=sigma, bb_mode=bb_mode, use_lagrange=use_lagrange).check()
+    assert np.array_equal(ex["idx"], op.idx)
+    assert np.array_equal(ex["kind"], op.kind)
+    mask = (op.link * (1 << np.arange(9))).sum(1)
+    assert np.array_equal(ex["link_mask"], mask)
+    assert np.allclose(ex["q"], op.q, rtol=0, atol=1e-12)
+    lag = op.kind == 1
+    assert np.array_equal(ex["lag_center"][lag], op.lag_center[lag])
+    assert np.allclose(ex["lag_h"][lag], op.lag_h[lag], rtol=1e-15, atol=0)
+    wls = op.kind == 0
+    if wls.any():
+        scale = np.abs(op.M[wls]).max(axis=(1, 2), keepdims=True)
+        assert np.abs(ex["M"][wls] - op.M[wls]).max() / scale.max() < 1e-10
+        assert (np.abs(ex["M"][wls] - op.M[wls]) / scale).max() < 1e-9
+    info = mlbm.stencils_info(st)
+    assert info["n_wls"] == int(wls.sum()) and info["n_lagrange"] == int(lag.sum())
+    assert info["n_links"] == int(op.link.sum())
+    return st, ex, op
+
+
+def test_builder_matches_oracle_poiseuille_channel():
+    _compare(I.poiseuille_channel(40, 50, 0.2, seed=1), K=12, s=1.0, bb_mode=1)
+
+
+@pytest.mark.parametrize("s", [1.0, 0.5])
+def test_builder_matches_oracle_lattices(s):
+    _compare(I.lattice(16, 12), K=12, s=s, bb_mode=1)
+    _, ex, _ = _compare(I.lattice_channel(8, 10, 0.5), K=16, s=s, bb_mode=0)
+    _compare(I.lattice_channel(8, 10, 0.0), K=16, s=s, bb_mode=1)
+
+
+def test_builder_matches_oracle_small_karman():
+    w = I.karman(seed=2, scale=0.25)
+    assert 10000 < w.n < 30000
+    _compare(w, K=16, s=1.0, bb_mode=0)
+
+
+def test_builder_matches_oracle_small_porous():
+    w = I.porous(seed=5, n_target=15000)
+    _compare(w, K=16, s=1.0, bb_mode=1)
+    _compare(w, K=16, s=0.25, bb_mode=1)
+
+
+def test_builder_errors():
+    w = I.lattice(6, 6)
+    with pytest.raises(mlbm.MlbmError) as e:
+        mlbm.build_stencils_for(w, K=10, s=1.0)
+    assert e.value.status == 1
+    with pytest.raises(mlbm.MlbmError) as e:
+        mlbm.build_stencils_for(w, K=12, s=-1.0)
+    assert e.value.status == 1
+    # collinear nodes: degenerate least squares
+    xy = np.stack([np.arange(20.0), np.full(20, 0.5)], 1)
+    with pytest.raises(mlbm.MlbmError) as e:
+        mlbm.build_stencils(xy, np.zeros(20, np.uint8), (0, 0, 20, 1), (0, 0, 2, 2), K=8, use_lagrange=False)
+    assert e.value.status == 2
+    # node inside a disk
+    xy = I.lattice(8, 8).xy
+    with pytest.raises(mlbm.MlbmError) as e:
+        mlbm.build_stencils(xy, np.zeros(64, np.uint8), (0, 0, 8, 8), (0, 0, 0, 0), disks=[[3.0, 3.0, 1.5]], K=12)
+    assert e.value.status == 8

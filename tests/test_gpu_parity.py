@@ -1,0 +1,313 @@
+"""GPU parity of the fused CUDA step (through the C ABI) against the FP64 oracle.
+
+Tolerances.  The GPU computes in FP32 with populations stored minus their
+weights; one step moves each stored value by at most a few ulp of the largest
+stencil term (|w_i| <= ~2, K <= 16 terms, values ~1e-2 after the shift), so
+the per-step absolute error on a population is ~1e-8.  Over n steps it grows
+at most linearly (the step is a contraction plus round-off), hence the
+population tolerance 2e-8 * (n + 10) used below.  For velocity fields the
+contract is the relative L2 error <= 1e-5 against the FP64 oracle for
+laminar cases.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_14789_gb300 import inputs as I
+from paper_2312_14789_gb300 import mlbm
+
+pytestmark = pytest.mark.gpu
+
+
+def pop_tol(n_steps):
+    return 2e-8 * (n_steps + 10)
+
+
+def random_populations(n, seed, amp=2e-3):
+    rng = np.random.default_rng(seed)
+    rho = 1 + 0.01 * rng.standard_normal(n)
+    ux = 0.02 * rng.standard_normal(n)
+    uy = 0.02 * rng.standard_normal(n)
+    return O.equilibrium(rho, ux, uy) + amp * I.uniform_noise((n, 9), seed + 1)
+
+
+def to_f32_state(f):
+    """The exact FP32 state the GPU stores (f - omega rounded to FP32)."""
+    _, W, _ = O.lattice_constants()
+    return (f - W).astype(np.float32).astype(np.float64) + W
+
+
+def gpu_ctx(w, K, s, bb_mode, params, sigma=0.7071067811865476, use_lagrange=True):
+    st = mlbm.build_stencils_for(w, K=K, s=s, sigma_factor=sigma, bb_mode=bb_mode, use_lagrange=use_lagrange)
+    return mlbm.init(st, params)
+
+
+# ----------------------------------------------------------------- plain MLBM
+def test_poiseuille_channel_2000_steps_matches_oracle():
+    """Plain MLBM Poiseuille case: 40x50 jittered grid, K=12, tau=0.8, s=1,
+    g=1e-6, 2000 steps; relative L2 velocity error <= 1e-5."""
+    w = I.poiseuille_channel(40, 50, 0.2, seed=1)
+    g = (1e-6, 0.0)
+    ctx = gpu_ctx(w, 12, 1.0, 1, mlbm.Params(mlbm.MODEL_BGK, 0.8, 0.0, *g))
+    mlbm.step(ctx, 2000)
+    rho, u = mlbm.macroscopics(ctx)
+    op = O.Operator(w, K=12, s=1.0, bb_mode=1).check()
+    f = O.run_bgk(op, O.equilibrium(np.ones(w.n), 0, 0), 0.8, g, 2000)
+    rho_o, ux_o, uy_o = O.macroscopics(f, g)
+    err = np.linalg.norm(np.stack([u[:, 0] - ux_o, u[:, 1] - uy_o])) / np.linalg.norm(np.stack([ux_o, uy_o]))
+    assert err <= 1e-5, err
+    assert np.abs(rho - rho_o).max() < 1e-6
+
+
+@pytest.mark.parametrize("case", ["lattice", "channel_halfway", "jittered", "karman_small", "porous_small"])
+def test_bgk_steps_match_oracle_elementwise(case):
+    if case == "lattice":
+        w, K, s, bb, tau, g = I.lattice(33, 17), 12, 1.0, 1, 0.7, (1e-5, -2e-6)
+    elif case == "channel_halfway":
+        w, K, s, bb, tau, g = I.lattice_channel(21, 13, 0.5), 16, 1.0, 0, 0.9, (1e-5, 0.0)
+    elif case == "jittered":
+        w, K, s, bb, tau, g = I.jittered_periodic(37, 29, 0.25, seed=4), 16, 0.8, 1, 0.75, (1e-5, 3e-6)
+    elif case == "karman_small":
+        w, K, s, bb, tau, g = I.karman(seed=2, scale=0.25), 16, 1.0, 0, 0.6, (0.0, 0.0)
+    else:
+        w, K, s, bb, tau, g = I.porous(seed=5, n_target=15000), 16, 0.5, 1, 0.8, (1e-5, 0.0)
+    f0 = to_f32_state(random_populations(w.n, 11))
+    ctx = gpu_ctx(w, K, s, bb, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, *g))
+    mlbm.set_populations(ctx, f0)
+    assert np.array_equal(mlbm.get_populations(ctx), f0)
+    op = O.Operator(w, K=K, s=s, bb_mode=bb).check()
+    f = f0
+    done = 0
+    for n_steps in (1, 9):
+        mlbm.step(ctx, n_steps)
+        for _ in range(n_steps):
+            f = O.bgk_step(op, f, tau, g)
+        done += n_steps
+        fg = mlbm.get_populations(ctx)
+        err = np.abs(fg - f).max()
+        assert err < pop_tol(done), (case, done, err)
+
+
+def test_regular_lattice_streaming_is_exact_in_fp32():
+    """s = h on a regular lattice: the Lagrange weights are exactly one-hot, so
+    with tau = 1 and no force the GPU step is the index shift of Eq. (1) followed
+    by the FP32 equilibrium; with g = 0 and a uniform state nothing changes."""
+    w = I.lattice(24, 16)
+    ctx = gpu_ctx(w, 12, 1.0, 1, mlbm.Params(mlbm.MODEL_BGK, 1.0, 0.0, 0.0, 0.0))
+    rng = np.random.default_rng(3)
+    # one moving population pattern, everything else at rest equilibrium
+    _, W, _ = O.lattice_constants()
+    f0 = np.tile(W, (w.n, 1))
+    f0[:, 1] += 1e-3 * rng.integers(0, 4, w.n)  # exact small binary fractions
+    mlbm.set_populations(ctx, f0)
+    op = O.Operator(w, K=12, s=1.0, bb_mode=1).check()
+    # streaming alone is exact: compare the moments the collision sees
+    mlbm.step(ctx, 1)
+    f1 = O.bgk_step(op, to_f32_state(f0), 1.0)
+    assert np.abs(mlbm.get_populations(ctx) - f1).max() < 1e-7
+    mass0 = f0.sum()
+    mlbm.step(ctx, 200)
+    assert abs(mlbm.get_populations(ctx).sum() - mass0) / mass0 < 1e-6
+
+
+def test_trt_matches_oracle():
+    w = I.poiseuille_channel(30, 20, 0.2, seed=7)
+    tau_p = 0.7
+    tau_m = 0.5 + (3 / 16) / (tau_p - 0.5)
+    g = (1e-5, 0.0)
+    ctx = gpu_ctx(w, 16, 1.0, 1, mlbm.Params(mlbm.MODEL_BGK, tau_p, tau_m, *g))
+    mlbm.step(ctx, 500)
+    op = O.Operator(w, K=16, s=1.0, bb_mode=1).check()
+    f = O.run_bgk(op, O.equilibrium(np.ones(w.n), 0, 0), tau_p, g, 500, tau_minus=tau_m)
+    _, ux, uy = O.macroscopics(f, g)
+    _, u = mlbm.macroscopics(ctx)
+    assert O.relative_l2(u[:, 0], ux) < 1e-5
+
+
+# --------------------------------------------------------------- tau = 1
+@pytest.mark.parametrize("case", ["lattice", "porous_small", "porous_small_s4", "channel_simple"])
+def test_tau1_steps_match_oracle(case):
+    if case == "lattice":
+        w, K, s, bb = I.lattice(20, 20), 12, 1.0, 1
+    elif case == "porous_small":
+        w, K, s, bb = I.porous(seed=6, n_target=20000), 16, 1.0, 1
+    elif case == "porous_small_s4":
+        w, K, s, bb = I.porous(seed=6, n_target=20000), 16, 0.25, 1
+    else:
+        w, K, s, bb = I.lattice_channel(15, 12, 0.5), 16, 1.0, 0
+    g = (1e-5, 2e-6)
+    rng = np.random.default_rng(2)
+    ru = np.stack([1 + 0.01 * rng.standard_normal(w.n), 0.01 * rng.standard_normal(w.n),
+                   0.01 * rng.standard_normal(w.n)], 1)
+    ru = np.stack([(ru[:, 0] - 1).astype(np.float32).astype(np.float64) + 1,
+                   ru[:, 1].astype(np.float32).astype(np.float64),
+                   ru[:, 2].astype(np.float32).astype(np.float64)], 1)
+    ctx = gpu_ctx(w, K, s, bb, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, *g))
+    mlbm.set_fields(ctx, ru)
+    op = O.Operator(w, K=K, s=s, bb_mode=bb).check()
+    a = ru
+    done = 0
+    for n_steps in (1, 9):
+        mlbm.step(ctx, n_steps)
+        for _ in range(n_steps):
+            a = O.mlbm1_step(op, a, g)
+        done += n_steps
+        b = mlbm.get_fields(ctx)
+        err = np.abs(b - a).max()
+        assert err < 5 * pop_tol(done), (case, done, err)
+
+
+def test_tau1_poiseuille_relative_l2():
+    w = I.poiseuille_channel(40, 50, 0.2, seed=1)
+    g = (1e-6, 0.0)
+    ctx = gpu_ctx(w, 12, 1.0, 1, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, *g))
+    mlbm.step(ctx, 2000)
+    ru = mlbm.get_fields(ctx)
+    op = O.Operator(w, K=12, s=1.0, bb_mode=1).check()
+    r0 = np.zeros((w.n, 3))
+    r0[:, 0] = 1
+    ro = O.run_mlbm1(op, r0, g, 2000)
+    assert O.relative_l2(ru[:, 1:], ro[:, 1:]) <= 1e-5
+
+
+# ------------------------------------------------------------ observables
+def test_force_and_permeability_match_oracle():
+    w = I.porous(seed=8, n_target=12000)
+    g = (1e-5, 0.0)
+    ctx = gpu_ctx(w, 16, 1.0, 1, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, *g))
+    mlbm.step(ctx, 300)
+    op = O.Operator(w, K=16, s=1.0, bb_mode=1).check()
+    r0 = np.zeros((w.n, 3))
+    r0[:, 0] = 1
+    ro = O.run_mlbm1(op, r0, g, 300)
+    fx, fy, cd, cl = mlbm.drag_lift(ctx, 1.0, 1.0)
+    ox, oy = O.force_mlbm1(op, ro, g)
+    scale = abs(ox) + abs(oy)
+    assert abs(fx - ox) / scale < 1e-4 and abs(fy - oy) / scale < 1e-4
+    pm = mlbm.permeability(ctx)
+    fluid = w.node_class != I.EQ
+    us, ui = O.mean_velocity(ro[:, 1], w.area, fluid, total_area=(w.box[2] - w.box[0]) * (w.box[3] - w.box[1]))
+    assert abs(pm["u_superficial"] / us - 1) < 1e-5
+    assert abs(pm["u_intrinsic"] / ui - 1) < 1e-5
+    assert abs(pm["k"] / O.permeability(us, 1.0, g[0]) - 1) < 1e-5
+    assert abs(pm["tortuosity"] / O.tortuosity(ro[:, 1], ro[:, 2], w.area) - 1) < 1e-5
+
+
+def test_karman_drag_matches_oracle():
+    w = I.karman(seed=2, scale=0.25)
+    U0 = w.meta["U0"]
+    ctx = gpu_ctx(w, 16, 1.0, 0, mlbm.Params(mlbm.MODEL_BGK, 0.56, 0.0, 0.0, 0.0))
+    mlbm.step(ctx, 200)
+    op = O.Operator(w, K=16, s=1.0, bb_mode=0).check()
+    f = O.run_bgk(op, O.equilibrium(np.ones(w.n), 0, 0), 0.56, (0, 0), 200)
+    fx, fy, cd, cl = mlbm.drag_lift(ctx, w.meta["D"], U0)
+    ox, oy = O.force_bgk(op, f)
+    assert abs(fx - ox) / abs(ox) < 1e-4
+    assert abs(fy - oy) < 1e-4 * abs(ox)
+    assert abs(cd - 2 * ox / (U0 ** 2 * w.meta["D"])) / abs(cd) < 1e-4
+
+
+# ------------------------------------------------------- full-size samples
+def _sample_targets(w, n_rand, seed, link_nodes=None):
+    rng = np.random.default_rng(seed)
+    t = rng.choice(w.n, size=n_rand, replace=False)
+    if link_nodes is not None and len(link_nodes):
+        t = np.concatenate([t, rng.choice(link_nodes, size=min(100, len(link_nodes)), replace=False)])
+    return np.unique(t)
+
+
+def test_karman_full_size_one_step_sampled():
+    """Cylinder channel at full size (~260k nodes, K=16, simple bounce-back):
+    one fused step from a random state, 400 sampled nodes (plus link nodes)
+    checked one by one against the oracle."""
+    w = I.karman(seed=2)
+    assert w.n > 200000
+    st = mlbm.build_stencils_for(w, K=16, s=1.0, bb_mode=0)
+    ex = mlbm.stencils_export(st)
+    ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, 0.56, 0.0, 0.0, 0.0))
+    f0 = to_f32_state(random_populations(w.n, 21))
+    mlbm.set_populations(ctx, f0)
+    mlbm.step(ctx, 1)
+    fg = mlbm.get_populations(ctx)
+    t = _sample_targets(w, 400, 5, np.nonzero(ex["link_mask"])[0])
+    op = O.Operator(w, K=16, s=1.0, bb_mode=0, targets=t).check()
+    assert np.array_equal(op.idx, ex["idx"][t])
+    fo = O.bgk_step(op, f0, 0.56)
+    assert np.abs(fg[t] - fo).max() < pop_tol(1)
+
+
+def test_porous_full_size_tau1_one_step_sampled():
+    """Porous box at full size (~1M nodes, K=16, interpolated bounce-back,
+    tau = 1): one step from a random state, sampled nodes against the oracle."""
+    w = I.porous(seed=3, n_target=1_000_000)
+    st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=1)
+    ex = mlbm.stencils_export(st)
+    g = (1e-5, 0.0)
+    ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, *g))
+    rng = np.random.default_rng(4)
+    ru = np.stack([1 + (0.01 * rng.standard_normal(w.n)).astype(np.float32).astype(np.float64),
+                   (0.01 * rng.standard_normal(w.n)).astype(np.float32).astype(np.float64),
+                   (0.01 * rng.standard_normal(w.n)).astype(np.float32).astype(np.float64)], 1)
+    mlbm.set_fields(ctx, ru)
+    mlbm.step(ctx, 1)
+    b = mlbm.get_fields(ctx)
+    t = _sample_targets(w, 400, 6, np.nonzero(ex["link_mask"])[0])
+    op = O.Operator(w, K=16, s=0.5, bb_mode=1, targets=t).check()
+    a = O.mlbm1_step(op, ru, g)
+    assert np.abs(b[t] - a).max() < 5 * pop_tol(1)
+
+
+# ------------------------------------------------------------ host features
+def test_save_load_continues_bitwise():
+    w = I.poiseuille_channel(20, 16, 0.2, seed=3)
+    p = mlbm.Params(mlbm.MODEL_BGK, 0.8, 0.0, 1e-5, 0.0)
+    a = gpu_ctx(w, 12, 1.0, 1, p)
+    mlbm.step(a, 100)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        mlbm.save(a, path)
+        mlbm.step(a, 100)
+        b = gpu_ctx(w, 12, 1.0, 1, p)
+        mlbm.load(b, path)
+        assert mlbm.step_count(b) == 100
+        mlbm.step(b, 100)
+    assert np.array_equal(mlbm.get_populations(a), mlbm.get_populations(b))
+
+
+def test_run_to_steady_poiseuille():
+    w = I.lattice_channel(4, 12, 0.5)
+    g, tau = 1e-5, 0.8
+    ctx = gpu_ctx(w, 16, 1.0, 0, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, g, 0.0))
+    steps = mlbm.run_to_steady(ctx, 1e-9, 500, 50000)
+    assert 0 < steps < 50000
+    _, u = mlbm.macroscopics(ctx)
+    uu = u[:, 0].reshape(12, 4)[:, 0]
+    d2 = uu[2:] - 2 * uu[1:-1] + uu[:-2]
+    nu = (tau - 0.5) / 3
+    assert np.allclose(d2, -g / nu, rtol=1e-3)
+
+
+def test_device_reduction_entry_point():
+    torch = pytest.importorskip("torch")
+    n = 300001
+    rng = np.random.default_rng(0)
+    h = {k: rng.uniform(0.5, 1.5, n).astype(np.float32) for k in ("rho", "ux", "uy", "area")}
+    mask = (rng.uniform(size=n) > 0.1).astype(np.uint8)
+    d = {k: torch.from_numpy(v).cuda() for k, v in h.items()}
+    dm = torch.from_numpy(mask).cuda()
+    ns = mlbm.reduce_scratch_doubles(n)
+    scratch = torch.empty(ns, dtype=torch.float64, device="cuda")
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
+    mlbm.reduce_fields_device(d["rho"].data_ptr(), d["ux"].data_ptr(), d["uy"].data_ptr(), d["area"].data_ptr(),
+                              dm.data_ptr(), n, scratch.data_ptr(), ns, out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    m = mask.astype(bool)
+    a, r, u, v = (h[k][m].astype(np.float64) for k in ("area", "rho", "ux", "uy"))
+    ref = [a.sum(), (r * a).sum(), (u * a).sum(), (v * a).sum(), (np.hypot(u, v) * a).sum(), ((u * u + v * v) * a).sum()]
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-12)
+    with pytest.raises(mlbm.MlbmError):
+        mlbm.reduce_fields_device(d["rho"].data_ptr(), d["ux"].data_ptr(), d["uy"].data_ptr(), d["area"].data_ptr(),
+                                  0, n, scratch.data_ptr(), ns - 1, out.data_ptr(), 0)
