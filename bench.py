@@ -3,8 +3,9 @@
 Workload: the Karman vortex street case -- a channel 22D x 4.1D with a
 cylinder of diameter D = 40 node spacings, ~260k scattered Poisson-disk nodes
 refined near the cylinder (seed 2), K = 16 least-squares stencils, BGK in
-FP32, Re = 100 at streaming distance s = 1 (tau = 0.56, U0 = 0.05), simple
-bounce-back on the cylinder, equilibrium inflow/outflow/side nodes.
+FP32, Re = 100 with streaming distance s = 1/2 node spacing (D = 80 lattice
+units, U0 = 0.05, tau = 0.62), simple bounce-back on the cylinder,
+equilibrium inflow/outflow/side nodes.
 One bench "step" = one MLBM time step over all nodes = one fused kernel
 launch.  L2 is flushed (a 512 MiB write) before every timed step, so each
 step reads its stencil data from HBM.
@@ -34,9 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "Mnode-updates/s (FP32, err vs FP64 stated); time-to-steady warm vs cold"
 UNIT = "Mnode-updates/s"
 WORKLOAD = {"workload": "karman_cylinder_channel", "nodes": None, "K": 16, "model": "BGK", "Re": 100,
-            "s": 1.0, "tau": 0.56, "D_spacings": 40, "seed": 2, "bounce_back": "simple",
+            "s": 0.5, "tau": 0.62, "D_spacings": 40, "D_lattice": 80, "seed": 2, "bounce_back": "simple",
             "l2": "flushed before every timed step (512 MiB write)"}
-TAU, RE, U0, D = 0.56, 100, 0.05, 40.0
+TAU, RE, U0, D, S_STREAM = 0.62, 100, 0.05, 40.0, 0.5
 PROFILE = os.path.join(ROOT, "profiles", "bgk_step_karman260k.md")
 
 
@@ -131,7 +132,7 @@ def oracle_sample_rate(w, n_sample, seed, min_seconds, max_reps):
     import oracle as O
     rng = np.random.default_rng(seed)
     t = np.sort(rng.choice(w.n, size=n_sample, replace=False))
-    op = O.Operator(w, K=16, s=1.0, bb_mode=0, targets=t).check()
+    op = O.Operator(w, K=16, s=S_STREAM, bb_mode=0, targets=t).check()
     f = O.equilibrium(np.ones(w.n), 0.0, 0.0)
     reps, elapsed = 0, 0.0
     while reps < max_reps and (elapsed < min_seconds or reps == 0):
@@ -152,7 +153,7 @@ def run_reference(args, rank, world):
     rng = np.random.default_rng(0)
     n_sample = 4096
     t = np.sort(rng.choice(w.n, size=n_sample, replace=False))
-    op = O.Operator(w, K=16, s=1.0, bb_mode=0, targets=t).check()
+    op = O.Operator(w, K=16, s=S_STREAM, bb_mode=0, targets=t).check()
     f = O.equilibrium(np.ones(w.n), 0.0, 0.0)
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -185,10 +186,11 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = make_workload()
-    st = mlbm.build_stencils_for(w, K=16, s=1.0, bb_mode=mlbm.BB_SIMPLE)
+    st = mlbm.build_stencils_for(w, K=16, s=S_STREAM, bb_mode=mlbm.BB_SIMPLE)
     info = mlbm.stencils_info(st)
     params = mlbm.Params(mlbm.MODEL_BGK, TAU, 0.0, 0.0, 0.0)
     ctx = mlbm.init(st, params)
+    variant, tune_ms = mlbm.autotune(ctx, 20)
     stream = torch.cuda.Stream()
     mlbm.set_stream(ctx, stream.cuda_stream)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 512 MiB > L2
@@ -244,7 +246,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = measured_traffic()
     cpu_val, cpu_threads, cpu_desc = oracle_sample_rate(w, 8192, 1, 10.0, 20000)
     cfg = dict(WORKLOAD, nodes=n, parallelism=f"replicas x{world}", n_wls=info["n_wls"], n_eq=info["n_eq"],
-               n_links=info["n_links"])
+               n_links=info["n_links"], kernel_variant=variant, autotune_ms_per_step=tune_ms)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak",

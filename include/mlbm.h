@@ -193,8 +193,8 @@ mlbm_status mlbm_macroscopics(mlbm_ctx* ctx, double* rho, double* u);
 
 /*
  * Force on all solids (momentum exchange over the bounce-back links, per unit
- * lattice area times area_x / s^2), as exchanged in the next streaming step
- * from the current state.  cd, cl = 2 F / (rho_ref u_ref^2 L_lb) with
+ * lattice area times area_x / s^2, relative to the rest state f = omega),
+ * as exchanged in the next streaming step from the current state.  cd, cl = 2 F / (rho_ref u_ref^2 L_lb) with
  * L_lb = ref_length / s, rho_ref = 1.  Any output pointer may be NULL.
  */
 mlbm_status mlbm_drag_lift(mlbm_ctx* ctx, double ref_length, double u_ref, double* fx, double* fy,
@@ -231,6 +231,30 @@ mlbm_status mlbm_load(mlbm_ctx* ctx, const char* path);
    timing is enabled (mlbm_set_timing(ctx, 1)); -1 when not measured. */
 mlbm_status mlbm_set_timing(mlbm_ctx* ctx, int enable);
 double mlbm_last_step_ms(const mlbm_ctx* ctx);
+
+/*
+ * Kernel variant of the fused step (all give the same results up to FP32
+ * summation order):
+ *   0    one thread per node, direct loads
+ *   1-3  two lanes per node (neighbour groups split, pair-shuffle reduction),
+ *        1 uncapped registers, 2 / 3 capped for 3 / 4 resident blocks of 256
+ *   4-7  persistent CTAs streaming the per-node matrix, indices and meta
+ *        bytes through a shared-memory ring filled by bulk async copies
+ *        (mbarrier pipeline), four lanes per node: 4 = 128-node tiles, 3
+ *        stages; 5 = 128-node tiles, 2 stages, 2 CTAs/SM; 6 = 64-node tiles,
+ *        3 stages; 7 = 64-node tiles, 2 stages (available for K = 12, 16, 24, 32)
+ *   8-10 persistent blocks walking node tiles that first bulk-prefetch the
+ *        matrix/index/meta rows of a later tile into L2 (no shared memory):
+ *        8 = two lanes per node, one round ahead; 9 = two lanes, two rounds
+ *        ahead; 10 = one lane per node, one round ahead
+ * The default is 4 when available, else 1.  mlbm_autotune times every
+ * available variant for steps_per_variant steps on the context's stream
+ * (state saved and restored, step count unchanged), keeps the fastest and
+ * returns its per-step time in *best_ms (may be NULL).
+ */
+mlbm_status mlbm_set_kernel_variant(mlbm_ctx* ctx, int variant);
+int mlbm_kernel_variant(const mlbm_ctx* ctx);
+mlbm_status mlbm_autotune(mlbm_ctx* ctx, int steps_per_variant, double* best_ms);
 
 /* ------------------------------------------------ device-level reductions */
 /*

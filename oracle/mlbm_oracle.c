@@ -547,7 +547,10 @@ void oracle_mlbm1_step(int64_t n, const double* ru_in, int64_t nt, const int64_t
  * exchange over bounce-back links): for each link (x, k) the population
  * f_{k'} that would leave into the solid returns as f_k(t+1, x); the solid
  * receives (f_{k'} + f_k) e_{k'} = 2 f_k(t+1, x) e_{k'} per unit lattice
- * area, weighted by the node area in lattice units, area_x / s^2.
+ * area, weighted by the node area in lattice units, area_x / s^2.  The rest
+ * state (f_k = omega_k, uniform pressure) exerts no net force on a closed
+ * body but its link sum on scattered nodes does not cancel exactly, so the
+ * exchange is taken relative to it: 2 (f_k(t+1, x) - omega_k) e_{k'}.
  * For the BGK state f_in[n][9]; link_mask[t][9] marks link directions.
  */
 void oracle_force_bgk(int64_t nt, const int64_t* targets, int K, const int64_t* idx, const double* W,
@@ -562,8 +565,8 @@ void oracle_force_bgk(int64_t nt, const int64_t* targets, int K, const int64_t* 
             int sk = src[9 * t + k];
             for (int j = 0; j < K; ++j) acc += W[(t * 9 + k) * K + j] * f_in[9 * idx[t * K + j] + sk];
             double a = area[i] / (s * s);
-            sx += 2.0 * acc * OEX[OOPP[k]] * a;
-            sy += 2.0 * acc * OEY[OOPP[k]] * a;
+            sx += 2.0 * (acc - oomega(k)) * OEX[OOPP[k]] * a;
+            sy += 2.0 * (acc - oomega(k)) * OEY[OOPP[k]] * a;
         }
     }
     *fx = sx;
@@ -590,8 +593,8 @@ void oracle_force_mlbm1(int64_t nt, const int64_t* targets, int K, const int64_t
             int sk = src[9 * t + k];
             double fk = oracle_feq(sk, r, ux, uy) + 0.5 * oracle_source(sk, r, ux, uy, gx, gy);
             double a = area[i] / (s * s);
-            sx += 2.0 * fk * OEX[OOPP[k]] * a;
-            sy += 2.0 * fk * OEY[OOPP[k]] * a;
+            sx += 2.0 * (fk - oomega(k)) * OEX[OOPP[k]] * a;
+            sy += 2.0 * (fk - oomega(k)) * OEY[OOPP[k]] * a;
         }
     }
     *fx = sx;

@@ -1,4 +1,5 @@
 // C-ABI glue: simulation contexts, state I/O, the step loop and observables.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -59,7 +60,8 @@ struct mlbm_ctx {
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = -1.0;
-    int block = 256;
+    int variant = 4;
+    int* err = nullptr;  // device error word of the bounded waits
     dev::Stencil S{};
     dev::Collide C{};
     std::vector<void*> allocations;
@@ -122,6 +124,29 @@ mlbm_status check_params(const mlbm_params* p) {
 
 mlbm_status sync(mlbm_ctx* c) {
     MLBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->err) {
+        int e = 0;
+        MLBM_CUDA(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e != 0) {
+            MLBM_CUDA(cudaMemset(c->err, 0, sizeof(int)));
+            return set_error(MLBM_E_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(e) +
+                                                 "); the step result is invalid");
+        }
+    }
+    return MLBM_OK;
+}
+
+mlbm_status launch_one_step(mlbm_ctx* c, int variant) {
+    const int a = c->cur, b = c->cur ^ 1;
+    const int model = c->params.model == MLBM_MODEL_BGK ? 0 : 1;
+    if (variant >= 4 && variant <= 7)
+        MLBM_CUDA(launch_step_tma(variant, model, c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->ruv[a], c->ruv[b],
+                                  c->C, c->err, c->stream));
+    else if (model == 0)
+        MLBM_CUDA(launch_bgk_step(c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->C, variant, c->stream));
+    else
+        MLBM_CUDA(launch_tau1_step(c->S, c->ruv[a], c->ruv[b], c->C, variant, c->stream));
+    c->cur = b;
     return MLBM_OK;
 }
 
@@ -155,10 +180,18 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
         harea[q] = (float)H.area[q];
         has2[q] = (float)(H.area[q] / (H.s * H.s));
         if (kind == kKindWls) {
-            for (int j = 0; j < K; ++j) {
-                hidx[(((size_t)(j / 4)) * np + q) * 4 + (j % 4)] = H.idx[(size_t)q * K + j];
+            // stencil slots in increasing node position: lanes of a warp that
+            // gather slot j of consecutive (Hilbert-ordered) nodes then touch
+            // nearby addresses; the matrix columns follow the same order
+            int order[32];
+            for (int j = 0; j < K; ++j) order[j] = j;
+            std::sort(order, order + K,
+                      [&](int a, int b) { return H.idx[(size_t)q * K + a] < H.idx[(size_t)q * K + b]; });
+            for (int jj = 0; jj < K; ++jj) {
+                const int j = order[jj];
+                hidx[(((size_t)(jj / 4)) * np + q) * 4 + (jj % 4)] = H.idx[(size_t)q * K + j];
                 for (int a = 0; a < 6; ++a)
-                    hM[(((size_t)(a * Kq + j / 4)) * np + q) * 4 + (j % 4)] = (float)H.M[((size_t)q * 6 + a) * K + j];
+                    hM[(((size_t)(a * Kq + jj / 4)) * np + q) * 4 + (jj % 4)] = (float)H.M[((size_t)q * 6 + a) * K + j];
             }
         } else if (kind == kKindLagrange) {
             for (int b = 0; b < 9; ++b) {
@@ -209,6 +242,9 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     c->scratch_len = std::max<int64_t>(6 * reduce_blocks(np), 2 * force_blocks(c->n_link_nodes));
     MLBM_TRY(dalloc(c, &c->scratch, c->scratch_len));
     MLBM_TRY(dalloc(c, &c->small, 16));
+    MLBM_TRY(dalloc(c, &c->err, 1));
+    MLBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    if (!tma_supported(Kq)) c->variant = 1;
     MLBM_TRY(upload(c, c->idx, hidx.data(), hidx.size() * 4));
     MLBM_TRY(upload(c, c->M, hM.data(), hM.size() * 4));
     MLBM_TRY(upload(c, c->meta, hmeta.data(), np));
@@ -361,14 +397,7 @@ mlbm_status mlbm_step(mlbm_ctx* c, int64_t n_steps) {
     if (n_steps < 0) return set_error(MLBM_E_INVALID, "step: negative step count");
     if (n_steps == 0) return MLBM_OK;
     if (c->timing) MLBM_CUDA(cudaEventRecord(c->ev0, c->stream));
-    for (int64_t t = 0; t < n_steps; ++t) {
-        const int a = c->cur, b = c->cur ^ 1;
-        if (c->params.model == MLBM_MODEL_BGK)
-            MLBM_CUDA(launch_bgk_step(c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->C, c->block, c->stream));
-        else
-            MLBM_CUDA(launch_tau1_step(c->S, c->ruv[a], c->ruv[b], c->C, c->block, c->stream));
-        c->cur = b;
-    }
+    for (int64_t t = 0; t < n_steps; ++t) MLBM_TRY(launch_one_step(c, c->variant));
     c->steps += n_steps;
     if (c->timing) {
         MLBM_CUDA(cudaEventRecord(c->ev1, c->stream));
@@ -514,6 +543,86 @@ mlbm_status mlbm_load(mlbm_ctx* c, const char* path) {
     }
     MLBM_TRY(sync(c));
     c->steps = hdr[3];
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_set_kernel_variant(mlbm_ctx* c, int variant) {
+    if (!c) return set_error(MLBM_E_INVALID, "set_kernel_variant: NULL context");
+    if (variant < 0 || variant > 10 || (variant >= 4 && variant <= 7 && !tma_supported(c->K / 4)))
+        return set_error(MLBM_E_INVALID, "set_kernel_variant: variant not available for this K");
+    c->variant = variant;
+    return MLBM_OK;
+}
+
+int mlbm_kernel_variant(const mlbm_ctx* c) { return c ? c->variant : -1; }
+
+mlbm_status mlbm_autotune(mlbm_ctx* c, int steps_per_variant, double* best_ms) {
+    if (!c || steps_per_variant < 1) return set_error(MLBM_E_INVALID, "autotune: bad arguments");
+    // keep the state: tuning steps run on a copy and the buffers are restored
+    const size_t np = (size_t)c->n_pad;
+    std::vector<void*> saved;
+    auto save_buf = [&](void* d, size_t bytes) -> mlbm_status {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return set_error(MLBM_E_OOM, "autotune: no room for a state copy");
+        }
+        saved.push_back(q);
+        MLBM_CUDA(cudaMemcpyAsync(q, d, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        return MLBM_OK;
+    };
+    const int cur0 = c->cur;
+    const int64_t steps0 = c->steps;
+    mlbm_status st = MLBM_OK;
+    if (c->params.model == MLBM_MODEL_BGK) {
+        st = save_buf(c->f8[cur0], 2 * np * sizeof(float4));
+        if (st == MLBM_OK) st = save_buf(c->f0[cur0], np * sizeof(float));
+    } else {
+        st = save_buf(c->ruv[cur0], np * sizeof(float4));
+    }
+    int best = c->variant;
+    double best_t = 1e30;
+    for (int v = 0; v <= 10 && st == MLBM_OK; ++v) {
+        if (v >= 4 && v <= 7 && !tma_supported(c->K / 4)) continue;
+        // one untimed warm-up launch, then the timed ones
+        st = launch_one_step(c, v);
+        if (st != MLBM_OK) {  // a variant that cannot launch here (resources) is skipped
+            (void)cudaGetLastError();
+            st = MLBM_OK;
+            continue;
+        }
+        if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) break;
+        for (int i = 0; i < steps_per_variant && st == MLBM_OK; ++i) st = launch_one_step(c, v);
+        if (st != MLBM_OK) break;
+        cudaEventRecord(c->ev1, c->stream);
+        if (cudaEventSynchronize(c->ev1) != cudaSuccess) {
+            st = set_error(MLBM_E_CUDA, "autotune: event wait failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        const double per = ms / steps_per_variant;
+        if (per < best_t) {
+            best_t = per;
+            best = v;
+        }
+    }
+    // restore
+    if (st == MLBM_OK) {
+        c->cur = cur0;
+        if (c->params.model == MLBM_MODEL_BGK) {
+            cudaMemcpyAsync(c->f8[cur0], saved[0], 2 * np * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemcpyAsync(c->f0[cur0], saved[1], np * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+        } else {
+            cudaMemcpyAsync(c->ruv[cur0], saved[0], np * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
+        }
+        st = sync(c);
+    }
+    for (void* q : saved) cudaFree(q);
+    c->steps = steps0;
+    if (st != MLBM_OK) return st;
+    c->variant = best;
+    if (best_ms) *best_ms = best_t;
     return MLBM_OK;
 }
 

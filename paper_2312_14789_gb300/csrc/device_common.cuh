@@ -71,5 +71,206 @@ __device__ __forceinline__ void basis_at(int k, float tt, float* pb) {
     pb[0] = 1.0f; pb[1] = ux; pb[2] = uy; pb[3] = ux * ux; pb[4] = ux * uy; pb[5] = uy * uy;
 }
 
+// ---------------------------------------------------------------- helpers
+// shifted equilibrium g_k = f_k^eq - omega_k of (rho = 1 + dr, u)
+__device__ __forceinline__ float geq(int k, float dr, float rho, float ux, float uy) {
+    const float eu = ex_of(k) * ux + ey_of(k) * uy;
+    const float usq = ux * ux + uy * uy;
+    return w_of(k) * (dr + rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq));
+}
+
+// second-order body-force source S_k (Guo form), F = rho a
+__device__ __forceinline__ float src(int k, float rho, float ux, float uy, float ax, float ay) {
+    const float ex = ex_of(k), ey = ey_of(k);
+    const float eu = ex * ux + ey * uy, ea = ex * ax + ey * ay;
+    return w_of(k) * rho * (3.0f * ea - 3.0f * (ux * ax + uy * ay) + 9.0f * eu * ea);
+}
+
+__device__ __forceinline__ void eq_populations(float dr, float ux, float uy, float* g) {
+    const float rho = 1.0f + dr;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = geq(k, dr, rho, ux, uy);
+}
+
+// single population k (1..8) of the BGK state at position j
+__device__ __forceinline__ float pop(const float4* f8, int j, int k) {
+    return __ldg(reinterpret_cast<const float*>(f8) + 8 * (size_t)j + (k - 1));
+}
+
+// Accumulate one stencil node's contribution for the 8 moving directions.
+// m0..m5: the node's column of M (units of s).  Weight of direction k is
+// p(-e_k)^T m with p = [1, x, y, x^2, x y, y^2].
+__device__ __forceinline__ void wls_acc(const float4* __restrict__ f8, int j, float m0, float m1, float m2, float m3,
+                                        float m4, float m5, const float4& oa, const float4& ob, float* acc) {
+    const float4 ra = __ldg(f8 + 2 * (size_t)j);
+    const float4 rb = __ldg(f8 + 2 * (size_t)j + 1);
+    const float4 a = make_float4(ra.x - oa.x, ra.y - oa.y, ra.z - oa.z, ra.w - oa.w);
+    const float4 b = make_float4(rb.x - ob.x, rb.y - ob.y, rb.z - ob.z, rb.w - ob.w);
+    const float A = m0 + m3, B = m0 + m5;
+    const float Cc = A + m5;
+    const float D = Cc + m4, E = Cc - m4;
+    const float G = m1 + m2, Hh = m1 - m2;
+    acc[0] = fmaf(A - m1, a.x, acc[0]);
+    acc[1] = fmaf(B - m2, a.y, acc[1]);
+    acc[2] = fmaf(A + m1, a.z, acc[2]);
+    acc[3] = fmaf(B + m2, a.w, acc[3]);
+    acc[4] = fmaf(D - G, b.x, acc[4]);
+    acc[5] = fmaf(E + Hh, b.y, acc[5]);
+    acc[6] = fmaf(D + G, b.z, acc[6]);
+    acc[7] = fmaf(E - Hh, b.w, acc[7]);
+}
+
+template <int KQ>
+__device__ __forceinline__ float wls_general(const Stencil& S, const float4* __restrict__ f8, int p, int k_src,
+                                             const float* pb) {
+    const float own = pop(f8, p, k_src);
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        const int4 id = __ldg(S.idx + (size_t)q * S.n_pad + p);
+        float4 m[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) m[a] = __ldg(S.M + (size_t)(a * KQ + q) * S.n_pad + p);
+        const int ids[4] = {id.x, id.y, id.z, id.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float* mc = reinterpret_cast<const float*>(m);
+            float w = 0.f;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) w = fmaf(pb[a], mc[4 * a + c], w);
+            acc = fmaf(w, pop(f8, ids[c], k_src) - own, acc);
+        }
+    }
+    return own + acc;
+}
+
+__device__ __forceinline__ void lag_block(const Stencil& S, int p, int* ids) {
+    const int4 i0 = __ldg(S.idx + p);
+    const int4 i1 = __ldg(S.idx + (size_t)S.n_pad + p);
+    const int4 i2 = __ldg(S.idx + 2 * (size_t)S.n_pad + p);
+    ids[0] = i0.x; ids[1] = i0.y; ids[2] = i0.z; ids[3] = i0.w;
+    ids[4] = i1.x; ids[5] = i1.y; ids[6] = i1.z; ids[7] = i1.w;
+    ids[8] = i2.x;
+}
+
+// Error-free FP32 transforms (Knuth TwoSum, FMA-based product error).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) + (hi, lo), not renormalised
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+    float e;
+    two_sum(ah, bh, sh, e);
+    sl = e + al + bl;
+}
+
+// Moments of the streamed populations g[0..8] (shifted), then the TRT update
+// (Eq. (3)-(5); BGK when omega_m == omega_p) of the pairs (k, k') = (1,3),
+// (2,4), (5,7), (6,8) selected by bit pr of pair_mask, and of k = 0 when
+// do_rest is set.  Lanes that share a node split the pairs between them.
+//
+// The update is formed as an increment g*_k = g_k + Delta_k computed only
+// from small quantities, so FP32 keeps mass and momentum to round-off of the
+// non-equilibrium part: the momentum-sized parts -- the pair differences
+// g_k - g_k' and J = rho u = sum g e + F/2 -- are carried as exact (hi, lo)
+// pairs, and the antisymmetric non-equilibrium part
+//   g_k^- - g_k^{eq-} = (g_k - g_k')/2 - 3 w_k e_k . J
+// is evaluated from them before rounding.  (With a plain FP32 u = j/rho +
+// g/2 the rounding of u acts as a steady momentum source that the slow
+// viscous modes amplify to ~1e-5 relative error in a Poiseuille channel.)
+__device__ __forceinline__ void collide_pairs(float* g, const Collide& C, unsigned pair_mask, bool do_rest) {
+    float dr = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dr += g[k];
+    const float rho = 1.0f + dr;
+    // exact pair differences d_pr = g_k - g_k'
+    float dh[4], dl[4];
+    two_sum(g[1], -g[3], dh[0], dl[0]);
+    two_sum(g[2], -g[4], dh[1], dl[1]);
+    two_sum(g[5], -g[7], dh[2], dl[2]);
+    two_sum(g[6], -g[8], dh[3], dl[3]);
+    const float Fx = rho * C.ax, Fy = rho * C.ay;
+    // J = rho u: Jx = d13 + d57 - d68 + Fx/2, Jy = d24 + d57 + d68 + Fy/2
+    float jxh, jxl, jyh, jyl;
+    df_add(dh[0], dl[0], dh[2], dl[2], jxh, jxl);
+    df_add(jxh, jxl, -dh[3], -dl[3], jxh, jxl);
+    df_add(jxh, jxl, 0.5f * Fx, 0.f, jxh, jxl);
+    df_add(dh[1], dl[1], dh[2], dl[2], jyh, jyl);
+    df_add(jyh, jyl, dh[3], dl[3], jyh, jyl);
+    df_add(jyh, jyl, 0.5f * Fy, 0.f, jyh, jyl);
+    const float inv = 1.0f / rho;
+    const float ux = jxh * inv, uy = jyh * inv;
+    const float usq = ux * ux + uy * uy;
+    const float ua = ux * C.ax + uy * C.ay;
+    if (do_rest) {
+        const float e0 = (4.0f / 9.0f) * (dr - rho * 1.5f * usq);
+        const float s0 = (4.0f / 9.0f) * rho * (-3.0f * ua);
+        g[0] = g[0] + (-C.omega_p * (g[0] - e0) + C.src_p * s0);
+    }
+#pragma unroll
+    for (int pr = 0; pr < 4; ++pr) {
+        if (!((pair_mask >> pr) & 1u)) continue;
+        const int k = pr < 2 ? pr + 1 : pr + 3;
+        const int kp = k + 2;
+        const float w = w_of(k);
+        const float ex = ex_of(k), ey = ey_of(k);
+        const float eu = ex * ux + ey * uy, ea = ex * C.ax + ey * C.ay;
+        const float gp = 0.5f * (g[k] + g[kp]);
+        const float ep = w * (dr + rho * (4.5f * eu * eu - 1.5f * usq));
+        // e_k . J as (hi, lo)
+        float eh, el;
+        if (pr == 0) { eh = jxh; el = jxl; }
+        else if (pr == 1) { eh = jyh; el = jyl; }
+        else if (pr == 2) df_add(jxh, jxl, jyh, jyl, eh, el);
+        else df_add(-jxh, -jxl, jyh, jyl, eh, el);
+        // g^- - g^{eq-} = c (a d - e.J): a = 3/2, c = 1/3 on the axes; a = 6, c = 1/12 on the diagonals
+        const float af = pr < 2 ? 1.5f : 6.0f;
+        const float cf = pr < 2 ? (1.0f / 3.0f) : (1.0f / 12.0f);
+        const float pa = __fmul_rn(af, dh[pr]);
+        const float pe = __fmaf_rn(af, dh[pr], -pa);
+        const float A = __fsub_rn(pa, eh) + ((pe + af * dl[pr]) - el);
+        const float nm = cf * A;
+        const float sp = w * rho * (9.0f * eu * ea - 3.0f * ua);
+        const float sm = w * rho * 3.0f * ea;
+        const float rp = -C.omega_p * (gp - ep) + C.src_p * sp;
+        const float rm = -C.omega_m * nm + C.src_m * sm;
+        g[k] = g[k] + (rp + rm);
+        g[kp] = g[kp] + (rp - rm);
+    }
+}
+
+// tau = 1: contribution of arriving direction k to the mass / momentum change.
+// The departure values are the node's own (dr, u) plus small interpolated
+// increments (a, bx, by); sk = k, or k' on a bounce-back link.  The large
+// term 3 w e . (rho u) of the own node cancels between opposite directions
+// and is kept out of the sums (its momentum, rho u, is added back
+// analytically); a link flips its sign, hence the -2 L term.  Accumulates
+// into dm (mass change), mx, my (momentum change).
+__device__ __forceinline__ void tau1_accumulate(int k, int sk, bool is_link, float a, float bx, float by,
+                                                float rhox, float uxx, float uyx, const Collide& C, float& dm,
+                                                float& mx, float& my) {
+    const float rd = rhox + a;
+    const float udx = uxx + bx, udy = uyx + by;
+    const float cx = a * uxx + rhox * bx + a * bx;
+    const float cy = a * uyx + rhox * by + a * by;
+    const float ex = ex_of(sk), ey = ey_of(sk), w = w_of(sk);
+    const float eu = ex * udx + ey * udy, usq = udx * udx + udy * udy;
+    const float ea = ex * C.ax + ey * C.ay;
+    float R = w * (a + 3.0f * (ex * cx + ey * cy) + rd * (4.5f * eu * eu - 1.5f * usq)) +
+              0.5f * w * rd * (3.0f * ea - 3.0f * (udx * C.ax + udy * C.ay) + 9.0f * eu * ea);
+    if (is_link) R -= 2.0f * 3.0f * w_of(k) * (ex_of(k) * rhox * uxx + ey_of(k) * rhox * uyx);
+    dm += R;
+    mx += R * ex_of(k);
+    my += R * ey_of(k);
+}
+
+template <int LPN>
+__device__ __forceinline__ void collide_part(float* g, const Collide& C, int h) {
+    if (LPN == 1) collide_pairs(g, C, 0xFu, true);
+    else collide_pairs(g, C, h == 0 ? 0x3u : 0xCu, h == 0);
+}
+
 }  // namespace dev
 }  // namespace mlbm

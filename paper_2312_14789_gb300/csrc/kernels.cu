@@ -13,6 +13,11 @@
 //
 // All population values are stored minus their weight omega_k (and rho as
 // rho - 1) so that FP32 keeps the small deviations that carry the flow.
+// Interpolation is centred on the node's own value, f(x_d) = f(x) +
+// sum_j w_j (f_j - f(x)), which equals sum_j w_j f_j because the weights sum
+// to one; with FP32 weights the sum is one only to ~1e-7, and the centred form
+// keeps that error off the mean value (it would otherwise act as a steady
+// mass/momentum source that the slow viscous modes amplify).
 #include <cstdio>
 
 #include "device_common.cuh"
@@ -21,130 +26,13 @@
 namespace mlbm {
 namespace dev {
 
-// ---------------------------------------------------------------- helpers
-// shifted equilibrium g_k = f_k^eq - omega_k of (rho = 1 + dr, u)
-__device__ __forceinline__ float geq(int k, float dr, float rho, float ux, float uy) {
-    const float eu = ex_of(k) * ux + ey_of(k) * uy;
-    const float usq = ux * ux + uy * uy;
-    return w_of(k) * (dr + rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq));
-}
-
-// second-order body-force source S_k (Guo form), F = rho a
-__device__ __forceinline__ float src(int k, float rho, float ux, float uy, float ax, float ay) {
-    const float ex = ex_of(k), ey = ey_of(k);
-    const float eu = ex * ux + ey * uy, ea = ex * ax + ey * ay;
-    return w_of(k) * rho * (3.0f * ea - 3.0f * (ux * ax + uy * ay) + 9.0f * eu * ea);
-}
-
-// TRT collision of shifted populations g[0..8] in place (BGK when omega_m == omega_p)
-__device__ __forceinline__ void collide(float* g, const Collide& C) {
-    float dr = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) dr += g[k];
-    const float rho = 1.0f + dr;
-    const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-    const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-    const float inv = 1.0f / rho;
-    const float ux = jx * inv + 0.5f * C.ax, uy = jy * inv + 0.5f * C.ay;
-    const float usq = ux * ux + uy * uy;
-    const float ua = ux * C.ax + uy * C.ay;
-    // k = 0
-    {
-        const float e0 = (4.0f / 9.0f) * (dr - rho * 1.5f * usq);
-        const float s0 = (4.0f / 9.0f) * rho * (-3.0f * ua);
-        g[0] = g[0] - C.omega_p * (g[0] - e0) + C.src_p * s0;
-    }
-    // pairs (k, k') = (1,3), (2,4), (5,7), (6,8)
-#pragma unroll
-    for (int pr = 0; pr < 4; ++pr) {
-        const int k = pr < 2 ? pr + 1 : pr + 3;
-        const int kp = k + 2;
-        const float w = w_of(k);
-        const float ex = ex_of(k), ey = ey_of(k);
-        const float eu = ex * ux + ey * uy, ea = ex * C.ax + ey * C.ay;
-        const float ep = w * (dr + rho * (4.5f * eu * eu - 1.5f * usq));
-        const float em = w * rho * 3.0f * eu;
-        const float sp = w * rho * (9.0f * eu * ea - 3.0f * ua);
-        const float sm = w * rho * 3.0f * ea;
-        const float gp = 0.5f * (g[k] + g[kp]), gm = 0.5f * (g[k] - g[kp]);
-        const float rp = -C.omega_p * (gp - ep) + C.src_p * sp;
-        const float rm = -C.omega_m * (gm - em) + C.src_m * sm;
-        g[k] = g[k] + rp + rm;
-        g[kp] = g[kp] + rp - rm;
-    }
-}
-
-__device__ __forceinline__ void eq_populations(float dr, float ux, float uy, float* g) {
-    const float rho = 1.0f + dr;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) g[k] = geq(k, dr, rho, ux, uy);
-}
-
-// single population k (1..8) of the BGK state at position j
-__device__ __forceinline__ float pop(const float4* f8, int j, int k) {
-    return __ldg(reinterpret_cast<const float*>(f8) + 8 * (size_t)j + (k - 1));
-}
-
-// Accumulate one stencil node's contribution for the 8 moving directions.
-// m0..m5: the node's column of M (units of s).  Weight of direction k is
-// p(-e_k)^T m with p = [1, x, y, x^2, x y, y^2].
-__device__ __forceinline__ void wls_acc(const float4* __restrict__ f8, int j, float m0, float m1, float m2, float m3,
-                                        float m4, float m5, float* acc) {
-    const float4 a = __ldg(f8 + 2 * (size_t)j);
-    const float4 b = __ldg(f8 + 2 * (size_t)j + 1);
-    const float A = m0 + m3, B = m0 + m5;
-    const float Cc = A + m5;
-    const float D = Cc + m4, E = Cc - m4;
-    const float G = m1 + m2, Hh = m1 - m2;
-    acc[0] = fmaf(A - m1, a.x, acc[0]);
-    acc[1] = fmaf(B - m2, a.y, acc[1]);
-    acc[2] = fmaf(A + m1, a.z, acc[2]);
-    acc[3] = fmaf(B + m2, a.w, acc[3]);
-    acc[4] = fmaf(D - G, b.x, acc[4]);
-    acc[5] = fmaf(E + Hh, b.y, acc[5]);
-    acc[6] = fmaf(D + G, b.z, acc[6]);
-    acc[7] = fmaf(E - Hh, b.w, acc[7]);
-}
-
-template <int KQ>
-__device__ __forceinline__ float wls_general(const Stencil& S, const float4* __restrict__ f8, int p, int k_src,
-                                             const float* pb) {
-    float acc = 0.f;
-#pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-        const int4 id = __ldg(S.idx + (size_t)q * S.n_pad + p);
-        float4 m[6];
-#pragma unroll
-        for (int a = 0; a < 6; ++a) m[a] = __ldg(S.M + (size_t)(a * KQ + q) * S.n_pad + p);
-        const int ids[4] = {id.x, id.y, id.z, id.w};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float* mc = reinterpret_cast<const float*>(m);
-            float w = 0.f;
-#pragma unroll
-            for (int a = 0; a < 6; ++a) w = fmaf(pb[a], mc[4 * a + c], w);
-            acc = fmaf(w, pop(f8, ids[c], k_src), acc);
-        }
-    }
-    return acc;
-}
-
-__device__ __forceinline__ void lag_block(const Stencil& S, int p, int* ids) {
-    const int4 i0 = __ldg(S.idx + p);
-    const int4 i1 = __ldg(S.idx + (size_t)S.n_pad + p);
-    const int4 i2 = __ldg(S.idx + 2 * (size_t)S.n_pad + p);
-    ids[0] = i0.x; ids[1] = i0.y; ids[2] = i0.z; ids[3] = i0.w;
-    ids[4] = i1.x; ids[5] = i1.y; ids[6] = i1.z; ids[7] = i1.w;
-    ids[8] = i2.x;
-}
-
 // ------------------------------------------------------------ BGK / TRT
-template <int KQ>
-__global__ void __launch_bounds__(256) bgk_step_kernel(Stencil S, const float4* __restrict__ f8in,
-                                                       const float* __restrict__ f0in, float4* __restrict__ f8out,
-                                                       float* __restrict__ f0out, Collide C) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= S.n) return;
+// LPN lanes (1 or 2) cooperate on one node: lane h takes the neighbour groups
+// q = h, h + LPN, ... and the partial sums are combined with a pair shuffle.
+template <int KQ, int LPN>
+__device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restrict__ f8in,
+                                         const float* __restrict__ f0in, float4* __restrict__ f8out,
+                                         float* __restrict__ f0out, const Collide& C, int p, int h, unsigned grp) {
     const uint8_t meta = S.meta[p];
     const int kind = meta & 3;
     float g[9];
@@ -158,17 +46,22 @@ __global__ void __launch_bounds__(256) bgk_step_kernel(Stencil S, const float4* 
         const float r = (kind == 1) ? __ldg(S.lag_r + p) : 0.f;
         const float cx = (kind == 1) ? (float)ex_of(meta >> 4) : 0.f;
         const float cy = (kind == 1) ? (float)ey_of(meta >> 4) : 0.f;
+        const float4 oa = __ldg(f8in + 2 * (size_t)p);
+        const float4 ob = __ldg(f8in + 2 * (size_t)p + 1);
         if (kind == 0) {
 #pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
-                float4 m[6];
+            for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
+                const int q = i * LPN + h;
+                if (q < KQ) {
+                    const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                    float4 m[6];
 #pragma unroll
-                for (int a = 0; a < 6; ++a) m[a] = ld_stream(S.M + (size_t)(a * KQ + q) * S.n_pad + p);
-                wls_acc(f8in, id.x, m[0].x, m[1].x, m[2].x, m[3].x, m[4].x, m[5].x, acc);
-                wls_acc(f8in, id.y, m[0].y, m[1].y, m[2].y, m[3].y, m[4].y, m[5].y, acc);
-                wls_acc(f8in, id.z, m[0].z, m[1].z, m[2].z, m[3].z, m[4].z, m[5].z, acc);
-                wls_acc(f8in, id.w, m[0].w, m[1].w, m[2].w, m[3].w, m[4].w, m[5].w, acc);
+                    for (int a = 0; a < 6; ++a) m[a] = ld_stream(S.M + (size_t)(a * KQ + q) * S.n_pad + p);
+                    wls_acc(f8in, id.x, m[0].x, m[1].x, m[2].x, m[3].x, m[4].x, m[5].x, oa, ob, acc);
+                    wls_acc(f8in, id.y, m[0].y, m[1].y, m[2].y, m[3].y, m[4].y, m[5].y, oa, ob, acc);
+                    wls_acc(f8in, id.z, m[0].z, m[1].z, m[2].z, m[3].z, m[4].z, m[5].z, oa, ob, acc);
+                    wls_acc(f8in, id.w, m[0].w, m[1].w, m[2].w, m[3].w, m[4].w, m[5].w, oa, ob, acc);
+                }
             }
         } else {
             int ids[9];
@@ -182,36 +75,44 @@ __global__ void __launch_bounds__(256) bgk_step_kernel(Stencil S, const float4* 
             lag3(-cy, y0[0], y0[1], y0[2]);
             lag3(r - cy, ym[0], ym[1], ym[2]);
 #pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const int j = ids[b * 3 + a];
-                    const float4 fa = __ldg(f8in + 2 * (size_t)j);
-                    const float4 fb = __ldg(f8in + 2 * (size_t)j + 1);
-                    acc[0] = fmaf(xp[a] * y0[b], fa.x, acc[0]);
-                    acc[1] = fmaf(x0[a] * yp[b], fa.y, acc[1]);
-                    acc[2] = fmaf(xm[a] * y0[b], fa.z, acc[2]);
-                    acc[3] = fmaf(x0[a] * ym[b], fa.w, acc[3]);
-                    acc[4] = fmaf(xp[a] * yp[b], fb.x, acc[4]);
-                    acc[5] = fmaf(xm[a] * yp[b], fb.y, acc[5]);
-                    acc[6] = fmaf(xm[a] * ym[b], fb.z, acc[6]);
-                    acc[7] = fmaf(xp[a] * ym[b], fb.w, acc[7]);
-                }
+            for (int bp = 0; bp < 9; ++bp) {
+                if (LPN == 2 && (bp & 1) != h) continue;
+                const int b = bp / 3, a = bp % 3;
+                const int j = ids[bp];
+                const float4 ra = __ldg(f8in + 2 * (size_t)j);
+                const float4 rb = __ldg(f8in + 2 * (size_t)j + 1);
+                const float4 fa = make_float4(ra.x - oa.x, ra.y - oa.y, ra.z - oa.z, ra.w - oa.w);
+                const float4 fb = make_float4(rb.x - ob.x, rb.y - ob.y, rb.z - ob.z, rb.w - ob.w);
+                acc[0] = fmaf(xp[a] * y0[b], fa.x, acc[0]);
+                acc[1] = fmaf(x0[a] * yp[b], fa.y, acc[1]);
+                acc[2] = fmaf(xm[a] * y0[b], fa.z, acc[2]);
+                acc[3] = fmaf(x0[a] * ym[b], fa.w, acc[3]);
+                acc[4] = fmaf(xp[a] * yp[b], fb.x, acc[4]);
+                acc[5] = fmaf(xm[a] * yp[b], fb.y, acc[5]);
+                acc[6] = fmaf(xm[a] * ym[b], fb.z, acc[6]);
+                acc[7] = fmaf(xp[a] * ym[b], fb.w, acc[7]);
+            }
         }
+        if (LPN == 2) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += __shfl_xor_sync(grp, acc[k], 1);
+        }
+        float own[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += own[k];
         if (meta & 4) {
+            // bounce-back links (rare): every lane of the node computes them
             const LinkRec L = S.links[S.link_slot[p]];
-            float over[8];
 #pragma unroll
             for (int k = 1; k < 9; ++k) {
-                over[k - 1] = acc[k - 1];
                 if (!((L.mask >> k) & 1u)) continue;
                 const int kp = opp_of(k);
                 if (S.bb_mode == 0) {
-                    over[k - 1] = pop(f8in, p, kp);
+                    acc[k - 1] = own[kp - 1];
                 } else if (kind == 0) {
                     float pb[6];
                     basis_at(k, L.t[k - 1], pb);
-                    over[k - 1] = wls_general<KQ>(S, f8in, p, kp, pb);
+                    acc[k - 1] = wls_general<KQ>(S, f8in, p, kp, pb);
                 } else {
                     int ids[9];
                     lag_block(S, p, ids);
@@ -219,25 +120,81 @@ __global__ void __launch_bounds__(256) bgk_step_kernel(Stencil S, const float4* 
                     float lx[3], ly[3];
                     lag3(tt * r * ex_of(k) - cx, lx[0], lx[1], lx[2]);
                     lag3(tt * r * ey_of(k) - cy, ly[0], ly[1], ly[2]);
+                    const float o = own[kp - 1];
                     float v = 0.f;
-#pragma unroll
                     for (int b = 0; b < 3; ++b)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) v = fmaf(lx[a] * ly[b], pop(f8in, ids[b * 3 + a], kp), v);
-                    over[k - 1] = v;
+                        for (int a = 0; a < 3; ++a) v = fmaf(lx[a] * ly[b], pop(f8in, ids[b * 3 + a], kp) - o, v);
+                    acc[k - 1] = o + v;
                 }
             }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = over[k];
         }
         g[0] = f0in[p];
 #pragma unroll
         for (int k = 1; k < 9; ++k) g[k] = acc[k - 1];
-        collide(g, C);
+        collide_part<LPN>(g, C, h);
     }
-    f8out[2 * (size_t)p] = make_float4(g[1], g[2], g[3], g[4]);
-    f8out[2 * (size_t)p + 1] = make_float4(g[5], g[6], g[7], g[8]);
-    f0out[p] = g[0];
+    if (LPN == 1 || h == 0) {
+        f8out[2 * (size_t)p] = make_float4(g[1], g[2], g[3], g[4]);
+        f0out[p] = g[0];
+    }
+    if (LPN == 1 || h == 1) f8out[2 * (size_t)p + 1] = make_float4(g[5], g[6], g[7], g[8]);
+}
+
+// Bulk prefetch of a node tile's stencil rows (matrix, indices, meta) into L2,
+// issued by the lanes of one warp; no registers or shared memory are used.
+__device__ __forceinline__ void prefetch_l2(const void* ptr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
+template <int KQ>
+__device__ __forceinline__ void prefetch_tile(const Stencil& S, int base, int tn, unsigned lane) {
+    if (base >= S.n) return;
+    const int nodes = min(tn, S.n_pad - base);
+    for (int c = (int)lane; c < 7 * KQ + 1; c += 32) {
+        if (c < 6 * KQ)
+            prefetch_l2(S.M + (size_t)c * S.n_pad + base, (uint32_t)nodes * 16u);
+        else if (c < 7 * KQ)
+            prefetch_l2(S.idx + (size_t)(c - 6 * KQ) * S.n_pad + base, (uint32_t)nodes * 16u);
+        else
+            prefetch_l2(S.meta + base, (uint32_t)((nodes + 15) / 16 * 16));
+    }
+}
+
+template <int KQ, int LPN, int MINB>
+__global__ void __launch_bounds__(256, MINB) bgk_step_kernel(Stencil S, const float4* __restrict__ f8in,
+                                                             const float* __restrict__ f0in,
+                                                             float4* __restrict__ f8out, float* __restrict__ f0out,
+                                                             Collide C) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = tid / LPN;
+    const int h = tid % LPN;
+    if (p >= S.n) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
+    bgk_node<KQ, LPN>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
+}
+
+// Persistent form: gridDim.x resident blocks walk the node tiles; before a
+// tile, warp 0 prefetches the stencil rows of the tile `dist` rounds ahead
+// into L2, so the streamed loads of later tiles hit L2 instead of waiting on
+// HBM while this tile gathers and collides.
+template <int KQ, int LPN, int MINB>
+__global__ void __launch_bounds__(256, MINB) bgk_step_persistent(Stencil S, const float4* __restrict__ f8in,
+                                                                 const float* __restrict__ f0in,
+                                                                 float4* __restrict__ f8out,
+                                                                 float* __restrict__ f0out, Collide C, int dist) {
+    constexpr int TN = 256 / LPN;
+    const int n_tiles = (S.n + TN - 1) / TN;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
+    const int h = threadIdx.x % LPN;
+    if (threadIdx.x < 32)
+        for (int d = 0; d < dist; ++d) prefetch_tile<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (threadIdx.x < 32) prefetch_tile<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
+        const int p = tile * TN + threadIdx.x / LPN;
+        if (p < S.n) bgk_node<KQ, LPN>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
+    }
 }
 
 // --------------------------------------------------------- tau = 1 (MLBM1)
@@ -252,18 +209,19 @@ __device__ __forceinline__ void eval_coeffs(const float (*c)[6], const float* pb
     }
 }
 
-template <int KQ>
-__global__ void __launch_bounds__(256) tau1_step_kernel(Stencil S, const float4* __restrict__ in,
-                                                        float4* __restrict__ out, Collide C) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= S.n) return;
+// LPN lanes per node: neighbour groups split as in the BGK kernel, the 18
+// fitted coefficients combined by a pair shuffle, the 8 directions split
+// (lane 0: k = 0..4, lane 1: k = 5..8) and the moment sums combined again.
+template <int KQ, int LPN>
+__device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __restrict__ in, float4* __restrict__ out,
+                                          const Collide& C, int p, int h, unsigned grp) {
     const uint8_t meta = S.meta[p];
     const int kind = meta & 3;
     if (kind == 2) {
-        out[p] = S.eqv[p];
+        if (h == 0) out[p] = S.eqv[p];
         return;
     }
-    const float4 me = in[p];
+    const float4 me = __ldg(in + p);
     float c[3][6];
     float4 v9[9];
     float r = 0.f, cx = 0.f, cy = 0.f;
@@ -273,24 +231,34 @@ __global__ void __launch_bounds__(256) tau1_step_kernel(Stencil S, const float4*
 #pragma unroll
             for (int a = 0; a < 6; ++a) c[f][a] = 0.f;
 #pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-            const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
-            float4 m[6];
+        for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
+            const int q = i * LPN + h;
+            if (q < KQ) {
+                const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                float4 m[6];
 #pragma unroll
-            for (int a = 0; a < 6; ++a) m[a] = ld_stream(S.M + (size_t)(a * KQ + q) * S.n_pad + p);
-            const int ids[4] = {id.x, id.y, id.z, id.w};
+                for (int a = 0; a < 6; ++a) m[a] = ld_stream(S.M + (size_t)(a * KQ + q) * S.n_pad + p);
+                const int ids[4] = {id.x, id.y, id.z, id.w};
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const float4 v = __ldg(in + ids[cc]);
-                const float* mc = reinterpret_cast<const float*>(m);
+                for (int cc = 0; cc < 4; ++cc) {
+                    const float4 rv = __ldg(in + ids[cc]);
+                    const float vx = rv.x - me.x, vy = rv.y - me.y, vz = rv.z - me.z;
+                    const float* mc = reinterpret_cast<const float*>(m);
 #pragma unroll
-                for (int a = 0; a < 6; ++a) {
-                    const float ma = mc[4 * a + cc];
-                    c[0][a] = fmaf(ma, v.x, c[0][a]);
-                    c[1][a] = fmaf(ma, v.y, c[1][a]);
-                    c[2][a] = fmaf(ma, v.z, c[2][a]);
+                    for (int a = 0; a < 6; ++a) {
+                        const float ma = mc[4 * a + cc];
+                        c[0][a] = fmaf(ma, vx, c[0][a]);
+                        c[1][a] = fmaf(ma, vy, c[1][a]);
+                        c[2][a] = fmaf(ma, vz, c[2][a]);
+                    }
                 }
             }
+        }
+        if (LPN == 2) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int a = 0; a < 6; ++a) c[f][a] += __shfl_xor_sync(grp, c[f][a], 1);
         }
     } else {
         int ids[9];
@@ -304,18 +272,17 @@ __global__ void __launch_bounds__(256) tau1_step_kernel(Stencil S, const float4*
     LinkRec L;
     L.mask = 0;
     if (meta & 4) L = S.links[S.link_slot[p]];
-    // k = 0 from the node itself
-    const float rho0 = 1.0f + me.x;
-    float dr = geq(0, me.x, rho0, me.y, me.z) + 0.5f * src(0, rho0, me.y, me.z, C.ax, C.ay);
-    float jx = 0.f, jy = 0.f;
+    const float rhox = 1.0f + me.x;
+    float dm = 0.f, mx = 0.f, my = 0.f;
+    if (LPN == 1 || h == 0)
+        dm = w_of(0) * rhox * (-1.5f * (me.y * me.y + me.z * me.z)) + 0.5f * src(0, rhox, me.y, me.z, C.ax, C.ay);
 #pragma unroll
     for (int k = 1; k < 9; ++k) {
+        if (LPN == 2 && ((k - 1) >> 2) != h) continue;
         const bool is_link = (L.mask >> k) & 1u;
         const int sk = is_link ? opp_of(k) : k;
-        float d[3];
-        if (is_link && S.bb_mode == 0) {
-            d[0] = me.x; d[1] = me.y; d[2] = me.z;
-        } else {
+        float d[3] = {0.f, 0.f, 0.f};  // increments over the node's own (dr, u, v)
+        if (!(is_link && S.bb_mode == 0)) {
             const float tt = is_link ? L.t[k - 1] : -1.0f;
             if (kind == 0) {
                 float pb[6];
@@ -325,28 +292,61 @@ __global__ void __launch_bounds__(256) tau1_step_kernel(Stencil S, const float4*
                 float lx[3], ly[3];
                 lag3(tt * r * ex_of(k) - cx, lx[0], lx[1], lx[2]);
                 lag3(tt * r * ey_of(k) - cy, ly[0], ly[1], ly[2]);
-                d[0] = d[1] = d[2] = 0.f;
 #pragma unroll
                 for (int b = 0; b < 3; ++b)
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const float w = lx[a] * ly[b];
                         const float4 v = v9[b * 3 + a];
-                        d[0] = fmaf(w, v.x, d[0]);
-                        d[1] = fmaf(w, v.y, d[1]);
-                        d[2] = fmaf(w, v.z, d[2]);
+                        d[0] = fmaf(w, v.x - me.x, d[0]);
+                        d[1] = fmaf(w, v.y - me.y, d[1]);
+                        d[2] = fmaf(w, v.z - me.z, d[2]);
                     }
             }
         }
-        const float rd = 1.0f + d[0];
-        const float fk = geq(sk, d[0], rd, d[1], d[2]) + 0.5f * src(sk, rd, d[1], d[2], C.ax, C.ay);
-        dr += fk;
-        jx += fk * ex_of(k);
-        jy += fk * ey_of(k);
+        tau1_accumulate(k, sk, is_link, d[0], d[1], d[2], rhox, me.y, me.z, C, dm, mx, my);
     }
-    const float rho = 1.0f + dr;
-    const float inv = 1.0f / rho;
-    out[p] = make_float4(dr, jx * inv + 0.5f * C.ax, jy * inv + 0.5f * C.ay, 0.f);
+    if (LPN == 2) {
+        dm += __shfl_xor_sync(grp, dm, 1);
+        mx += __shfl_xor_sync(grp, mx, 1);
+        my += __shfl_xor_sync(grp, my, 1);
+    }
+    if (LPN == 1 || h == 0) {
+        const float rho = rhox + dm;
+        const float inv = 1.0f / rho;
+        const float nux = me.y + (mx + 0.5f * rho * C.ax - dm * me.y) * inv;
+        const float nuy = me.z + (my + 0.5f * rho * C.ay - dm * me.z) * inv;
+        out[p] = make_float4(me.x + dm, nux, nuy, 0.f);
+    }
+}
+
+template <int KQ, int LPN, int MINB>
+__global__ void __launch_bounds__(256, MINB) tau1_step_kernel(Stencil S, const float4* __restrict__ in,
+                                                              float4* __restrict__ out, Collide C) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = tid / LPN;
+    const int h = tid % LPN;
+    if (p >= S.n) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
+    tau1_node<KQ, LPN>(S, in, out, C, p, h, grp);
+}
+
+template <int KQ, int LPN, int MINB>
+__global__ void __launch_bounds__(256, MINB) tau1_step_persistent(Stencil S, const float4* __restrict__ in,
+                                                                  float4* __restrict__ out, Collide C, int dist) {
+    constexpr int TN = 256 / LPN;
+    const int n_tiles = (S.n + TN - 1) / TN;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
+    const int h = threadIdx.x % LPN;
+    if (threadIdx.x < 32)
+        for (int d = 0; d < dist; ++d) prefetch_tile<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (threadIdx.x < 32) prefetch_tile<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
+        const int p = tile * TN + threadIdx.x / LPN;
+        if (p < S.n) tau1_node<KQ, LPN>(S, in, out, C, p, h, grp);
+    }
 }
 
 // ------------------------------------------------------------- state I/O
@@ -463,7 +463,9 @@ __global__ void macroscopics_tau1(int n, const int* __restrict__ perm, const flo
 
 // --------------------------------------------------------- wall force
 // Momentum handed to the solids in the next streaming step: sum over links of
-// 2 f_k(t+1, x) e_{k'} area_x / s^2, per-block FP64 partials (fixed order).
+// 2 (f_k(t+1, x) - omega_k) e_{k'} area_x / s^2 (relative to the rest state,
+// whose uniform pressure exerts no net force on a closed body), per-block
+// FP64 partials added in a fixed order.
 template <int KQ>
 __global__ void __launch_bounds__(128) force_kernel(Stencil S, int model, int n_link_nodes,
                                                     const int* __restrict__ link_nodes,
@@ -501,7 +503,6 @@ __global__ void __launch_bounds__(128) force_kernel(Stencil S, int model, int n_
                     for (int b = 0; b < 3; ++b)
                         for (int aa = 0; aa < 3; ++aa) val = fmaf(lx[aa] * ly[b], pop(st8, ids[b * 3 + aa], kp), val);
                 }
-                val += w_of(kp);
             } else {
                 float d[3];
                 if (S.bb_mode == 0) {
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(128) force_kernel(Stencil S, int model, int n_
                         }
                 }
                 const float rd = 1.0f + d[0];
-                val = geq(kp, d[0], rd, d[1], d[2]) + 0.5f * src(kp, rd, d[1], d[2], C.ax, C.ay) + w_of(kp);
+                val = geq(kp, d[0], rd, d[1], d[2]) + 0.5f * src(kp, rd, d[1], d[2], C.ax, C.ay);
             }
             fx += 2.0 * (double)val * ex_of(kp) * a;
             fy += 2.0 * (double)val * ey_of(kp) * a;
@@ -684,17 +685,54 @@ inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
         default: return cudaErrorInvalidValue;           \
     }
 
+// grid of exactly the resident blocks (occupancy API), at most one per tile
+template <class F>
+cudaError_t run_persistent(const void* fn, int tile_nodes, int n, cudaStream_t, F launch) {
+    int dev_id = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    if (e != cudaSuccess) return e;
+    const int tiles = (n + tile_nodes - 1) / tile_nodes;
+    const int grid = std::max(1, std::min(tiles, sms * std::max(per_sm, 1)));
+    launch(grid);
+    return cudaSuccess;
+}
+
+// variant v: lanes per node and minimum resident blocks (register cap)
+//   0: 1 lane, no cap   1: 2 lanes, no cap   2: 2 lanes, >= 3 blocks of 256
+//   3: 2 lanes, >= 4 blocks of 256
 cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,
-                            float* f0out, const dev::Collide& C, int block, cudaStream_t st) {
+                            float* f0out, const dev::Collide& C, int variant, cudaStream_t st) {
     if (S.n == 0) return cudaSuccess;
-    MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C)));
+    const int block = 256;
+    switch (variant) {
+        case 0: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 1, 1><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 1: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 2, 1><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 2: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 2, 3><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 3: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 2, 4><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 8: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        case 9: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 2); }))); break;
+        case 10: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 1>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 1><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C, int block,
+cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C, int variant,
                              cudaStream_t st) {
     if (S.n == 0) return cudaSuccess;
-    MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C)));
+    const int block = 256;
+    switch (variant) {
+        case 0: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 1, 1><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
+        case 1: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 2, 1><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, in, out, C))); break;
+        case 2: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 2, 3><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, in, out, C))); break;
+        case 3: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 2, 4><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, in, out, C))); break;
+        case 8: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
+        case 9: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, in, out, C, 2); }))); break;
+        case 10: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 1>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 1><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -10,8 +10,8 @@
 namespace mlbm {
 
 cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,
-                            float* f0out, const dev::Collide& C, int block, cudaStream_t st);
-cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C, int block,
+                            float* f0out, const dev::Collide& C, int variant, cudaStream_t st);
+cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C, int variant,
                              cudaStream_t st);
 cudaError_t launch_set_bgk(int n, const int* perm, const double* f, float4* f8, float* f0, cudaStream_t st);
 cudaError_t launch_get_bgk(int n, const int* perm, const float4* f8, const float* f0, double* f, cudaStream_t st);
@@ -22,6 +22,11 @@ cudaError_t launch_get_tau1(int n, const int* perm, const float4* s, double* ru,
 cudaError_t launch_macroscopics(int model, int n, const int* perm, const float4* f8, const float* f0,
                                 const float4* ruv, float ax, float ay, float* rho, float* ux, float* uy, double* ru,
                                 cudaStream_t st);
+// persistent bulk-copy pipelined step (kernels_tma.cu), variants 4..7
+bool tma_supported(int Kq);
+cudaError_t launch_step_tma(int variant, int model, const dev::Stencil& S, const float4* f8in, const float* f0in,
+                            float4* f8out, float* f0out, const float4* rin, float4* rout, const dev::Collide& C,
+                            int* err, cudaStream_t st);
 int force_blocks(int n_link_nodes);
 cudaError_t launch_force(const dev::Stencil& S, int model, int n_link_nodes, const int* link_nodes,
                          const float* area_over_s2, const float4* f8, const float4* ruv, const dev::Collide& C,

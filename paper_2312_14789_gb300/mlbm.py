@@ -83,6 +83,9 @@ def lib():
                 "mlbm_load": (st, [_vp, ctypes.c_char_p]),
                 "mlbm_set_timing": (st, [_vp, _i32]),
                 "mlbm_last_step_ms": (_dbl, [_vp]),
+                "mlbm_set_kernel_variant": (st, [_vp, _i32]),
+                "mlbm_kernel_variant": (_i32, [_vp]),
+                "mlbm_autotune": (st, [_vp, _i32, _vp]),
                 "mlbm_reduce_scratch_doubles": (_i64, [_i64]),
                 "mlbm_reduce_fields_device": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
                 "mlbm_last_error": (ctypes.c_char_p, []),
@@ -278,6 +281,21 @@ def set_timing(ctx: Context, enable: bool):
 
 def last_step_ms(ctx: Context) -> float:
     return float(lib().mlbm_last_step_ms(ctx.handle))
+
+
+def set_kernel_variant(ctx: Context, variant: int):
+    _check(lib().mlbm_set_kernel_variant(ctx.handle, int(variant)))
+
+
+def kernel_variant(ctx: Context) -> int:
+    return int(lib().mlbm_kernel_variant(ctx.handle))
+
+
+def autotune(ctx: Context, steps_per_variant: int = 20) -> tuple:
+    """Pick the fastest kernel variant on this context; returns (variant, ms/step)."""
+    ms = ctypes.c_double()
+    _check(lib().mlbm_autotune(ctx.handle, int(steps_per_variant), ctypes.byref(ms)))
+    return kernel_variant(ctx), ms.value
 
 
 def reduce_scratch_doubles(n: int) -> int:

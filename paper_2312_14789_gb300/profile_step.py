@@ -3,7 +3,7 @@
     python -m paper_2312_14789_gb300.profile_step --workload karman --steps 3
     python -m paper_2312_14789_gb300.profile_step --workload porous --steps 3
 
-karman: the ~260k-node cylinder channel, BGK, K = 16 (the benchmark case);
+karman: the ~260k-node cylinder channel, BGK, K = 16, s = 1/2 (the benchmark case);
 porous: the ~1M-node porous box, tau = 1, K = 16, s = 1/2.
 No timing is reported; the process exits 0 when the steps ran.
 """
@@ -26,18 +26,24 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--n-target", type=int, default=1_000_000)
+    ap.add_argument("--variant", type=int, default=-1, help="kernel variant (-1: autotune)")
     args = ap.parse_args()
     if args.workload == "karman":
         w = I.karman(seed=2)
-        st = mlbm.build_stencils_for(w, K=16, s=1.0, bb_mode=mlbm.BB_SIMPLE)
-        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, 0.56, 0.0, 0.0, 0.0))
+        st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=mlbm.BB_SIMPLE)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, 0.62, 0.0, 0.0, 0.0))
     else:
         w = I.porous(seed=3, n_target=args.n_target)
         st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=mlbm.BB_INTERPOLATED)
         ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, 1e-6, 0.0))
+    if args.variant >= 0:
+        mlbm.set_kernel_variant(ctx, args.variant)
+    else:
+        mlbm.autotune(ctx, 10)
     mlbm.step(ctx, args.warmup + args.steps)
     rho, _ = mlbm.macroscopics(ctx)
-    print(f"{args.workload}: {w.n} nodes, {args.warmup + args.steps} steps, mean rho {rho.mean():.6f}")
+    print(f"{args.workload}: {w.n} nodes, variant {mlbm.kernel_variant(ctx)}, {args.warmup + args.steps} steps, "
+          f"mean rho {rho.mean():.6f}")
 
 
 if __name__ == "__main__":
