@@ -190,7 +190,7 @@ def run_ours(args, rank, world, local_rank):
     info = mlbm.stencils_info(st)
     params = mlbm.Params(mlbm.MODEL_BGK, TAU, 0.0, 0.0, 0.0)
     ctx = mlbm.init(st, params)
-    variant, tune_ms = mlbm.autotune(ctx, 20)
+    variant, tune_ms = mlbm.autotune(ctx, 20, flush_l2=True)
     stream = torch.cuda.Stream()
     mlbm.set_stream(ctx, stream.cuda_stream)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 512 MiB > L2

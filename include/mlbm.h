@@ -242,11 +242,14 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        bytes through a shared-memory ring filled by bulk async copies
  *        (mbarrier pipeline), four lanes per node: 4 = 128-node tiles, 3
  *        stages; 5 = 128-node tiles, 2 stages, 2 CTAs/SM; 6 = 64-node tiles,
- *        3 stages; 7 = 64-node tiles, 2 stages (available for K = 12, 16, 24, 32)
+ *        3 stages; 7 = 64-node tiles, 2 stages
  *   8-10 persistent blocks walking node tiles that first bulk-prefetch the
  *        matrix/index/meta rows of a later tile into L2 (no shared memory):
  *        8 = two lanes per node, one round ahead; 9 = two lanes, two rounds
  *        ahead; 10 = one lane per node, one round ahead
+ *   11   one lane per node, registers capped for 2 resident blocks of 256
+ *   12-13 as 10 with registers capped for 2 / 3 resident blocks of 256
+ * Variants 4 and up are available for K = 12, 16, 24 and 32.
  * The default is 4 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream
  * (state saved and restored, step count unchanged), keeps the fastest and
@@ -255,6 +258,10 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
 mlbm_status mlbm_set_kernel_variant(mlbm_ctx* ctx, int variant);
 int mlbm_kernel_variant(const mlbm_ctx* ctx);
 mlbm_status mlbm_autotune(mlbm_ctx* ctx, int steps_per_variant, double* best_ms);
+/* As mlbm_autotune; with flush_l2 != 0 every timed step is preceded by a
+   512 MiB device write (a temporary buffer) so that steps are timed with a
+   cold L2, and each step is timed on its own. */
+mlbm_status mlbm_autotune_ex(mlbm_ctx* ctx, int steps_per_variant, int flush_l2, double* best_ms);
 
 /* ------------------------------------------------ device-level reductions */
 /*

@@ -190,8 +190,13 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
             for (int jj = 0; jj < K; ++jj) {
                 const int j = order[jj];
                 hidx[(((size_t)(jj / 4)) * np + q) * 4 + (jj % 4)] = H.idx[(size_t)q * K + j];
+                double m[6];
+                for (int a = 0; a < 6; ++a) m[a] = H.M[((size_t)q * 6 + a) * K + j];
+                // D2Q9 departure basis (see device_common.cuh), formed in FP64
+                const double t[6] = {m[0] + m[3], m[0] + m[5], m[0] + m[3] + m[4] + m[5], m[0] + m[3] - m[4] + m[5],
+                                     m[1], m[2]};
                 for (int a = 0; a < 6; ++a)
-                    hM[(((size_t)(a * Kq + jj / 4)) * np + q) * 4 + (jj % 4)] = (float)H.M[((size_t)q * 6 + a) * K + j];
+                    hM[(((size_t)(a * Kq + jj / 4)) * np + q) * 4 + (jj % 4)] = (float)t[a];
             }
         } else if (kind == kKindLagrange) {
             for (int b = 0; b < 9; ++b) {
@@ -548,7 +553,7 @@ mlbm_status mlbm_load(mlbm_ctx* c, const char* path) {
 
 mlbm_status mlbm_set_kernel_variant(mlbm_ctx* c, int variant) {
     if (!c) return set_error(MLBM_E_INVALID, "set_kernel_variant: NULL context");
-    if (variant < 0 || variant > 10 || (variant >= 4 && variant <= 7 && !tma_supported(c->K / 4)))
+    if (variant < 0 || variant > 13 || (variant >= 4 && !tma_supported(c->K / 4)))
         return set_error(MLBM_E_INVALID, "set_kernel_variant: variant not available for this K");
     c->variant = variant;
     return MLBM_OK;
@@ -557,7 +562,24 @@ mlbm_status mlbm_set_kernel_variant(mlbm_ctx* c, int variant) {
 int mlbm_kernel_variant(const mlbm_ctx* c) { return c ? c->variant : -1; }
 
 mlbm_status mlbm_autotune(mlbm_ctx* c, int steps_per_variant, double* best_ms) {
+    return mlbm_autotune_ex(c, steps_per_variant, 0, best_ms);
+}
+
+mlbm_status mlbm_autotune_ex(mlbm_ctx* c, int steps_per_variant, int flush_l2, double* best_ms) {
     if (!c || steps_per_variant < 1) return set_error(MLBM_E_INVALID, "autotune: bad arguments");
+    // optional L2 flush between timed steps: a 512 MiB device buffer rewritten
+    // before every step, so each timed step reads its stencil data from HBM
+    void* flush = nullptr;
+    const size_t flush_bytes = size_t(512) << 20;
+    if (flush_l2 && cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return set_error(MLBM_E_OOM, "autotune: no room for the L2 flush buffer");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (flush_l2) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+    }
     // keep the state: tuning steps run on a copy and the buffers are restored
     const size_t np = (size_t)c->n_pad;
     std::vector<void*> saved;
@@ -582,8 +604,8 @@ mlbm_status mlbm_autotune(mlbm_ctx* c, int steps_per_variant, double* best_ms) {
     }
     int best = c->variant;
     double best_t = 1e30;
-    for (int v = 0; v <= 10 && st == MLBM_OK; ++v) {
-        if (v >= 4 && v <= 7 && !tma_supported(c->K / 4)) continue;
+    for (int v = 0; v <= 13 && st == MLBM_OK; ++v) {
+        if (v >= 4 && !tma_supported(c->K / 4)) continue;
         // one untimed warm-up launch, then the timed ones
         st = launch_one_step(c, v);
         if (st != MLBM_OK) {  // a variant that cannot launch here (resources) is skipped
@@ -591,17 +613,37 @@ mlbm_status mlbm_autotune(mlbm_ctx* c, int steps_per_variant, double* best_ms) {
             st = MLBM_OK;
             continue;
         }
-        if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) break;
-        for (int i = 0; i < steps_per_variant && st == MLBM_OK; ++i) st = launch_one_step(c, v);
-        if (st != MLBM_OK) break;
-        cudaEventRecord(c->ev1, c->stream);
-        if (cudaEventSynchronize(c->ev1) != cudaSuccess) {
-            st = set_error(MLBM_E_CUDA, "autotune: event wait failed");
-            break;
+        double per = 0.0;
+        if (flush_l2) {
+            double tot = 0.0;
+            for (int i = 0; i < steps_per_variant && st == MLBM_OK; ++i) {
+                cudaMemsetAsync(flush, i & 0xff, flush_bytes, c->stream);
+                cudaEventRecord(e0, c->stream);
+                st = launch_one_step(c, v);
+                cudaEventRecord(e1, c->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = set_error(MLBM_E_CUDA, "autotune: event wait failed");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tot += ms;
+            }
+            if (st != MLBM_OK) break;
+            per = tot / steps_per_variant;
+        } else {
+            if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) break;
+            for (int i = 0; i < steps_per_variant && st == MLBM_OK; ++i) st = launch_one_step(c, v);
+            if (st != MLBM_OK) break;
+            cudaEventRecord(c->ev1, c->stream);
+            if (cudaEventSynchronize(c->ev1) != cudaSuccess) {
+                st = set_error(MLBM_E_CUDA, "autotune: event wait failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+            per = ms / steps_per_variant;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-        const double per = ms / steps_per_variant;
         if (per < best_t) {
             best_t = per;
             best = v;
@@ -619,6 +661,9 @@ mlbm_status mlbm_autotune(mlbm_ctx* c, int steps_per_variant, double* best_ms) {
         st = sync(c);
     }
     for (void* q : saved) cudaFree(q);
+    if (flush) cudaFree(flush);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     c->steps = steps0;
     if (st != MLBM_OK) return st;
     c->variant = best;

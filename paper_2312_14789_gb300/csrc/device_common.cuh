@@ -97,27 +97,42 @@ __device__ __forceinline__ float pop(const float4* f8, int j, int k) {
     return __ldg(reinterpret_cast<const float*>(f8) + 8 * (size_t)j + (k - 1));
 }
 
-// Accumulate one stencil node's contribution for the 8 moving directions.
-// m0..m5: the node's column of M (units of s).  Weight of direction k is
-// p(-e_k)^T m with p = [1, x, y, x^2, x y, y^2].
-__device__ __forceinline__ void wls_acc(const float4* __restrict__ f8, int j, float m0, float m1, float m2, float m3,
-                                        float m4, float m5, const float4& oa, const float4& ob, float* acc) {
+// The device keeps each node's 6 x K least-squares matrix (units of s) in
+// the basis the D2Q9 departure points need: with m_0..m_5 the rows of M for
+// p = [1, x, y, x^2, x y, y^2], the stored rows are
+//   U = m0 + m3, V = m0 + m5, W = m0 + m3 + m4 + m5, W' = m0 + m3 - m4 + m5, m1, m2,
+// so the weight of direction k at offset -e_k is one add or subtract:
+//   w1 = U - m1, w3 = U + m1, w2 = V - m2, w4 = V + m2,
+//   w5 = W - (m1 + m2), w7 = W + (m1 + m2), w6 = W' + (m1 - m2), w8 = W' - (m1 - m2).
+// unbasis() recovers m0..m5 for departure points elsewhere (bounce-back).
+__device__ __forceinline__ void unbasis(const float* t, float* m) {
+    const float s = 0.5f * (t[2] + t[3]);
+    m[0] = (t[0] + t[1]) - s;
+    m[1] = t[4];
+    m[2] = t[5];
+    m[3] = t[0] - m[0];
+    m[4] = 0.5f * (t[2] - t[3]);
+    m[5] = t[1] - m[0];
+}
+
+// Accumulate one stencil node's contribution (centred on the node's own
+// populations oa, ob) for the 8 moving directions; U..m2 is the node's
+// column of the stored matrix.
+__device__ __forceinline__ void wls_acc(const float4* __restrict__ f8, int j, float U, float V, float W, float Wp,
+                                        float m1, float m2, const float4& oa, const float4& ob, float* acc) {
     const float4 ra = __ldg(f8 + 2 * (size_t)j);
     const float4 rb = __ldg(f8 + 2 * (size_t)j + 1);
-    const float4 a = make_float4(ra.x - oa.x, ra.y - oa.y, ra.z - oa.z, ra.w - oa.w);
-    const float4 b = make_float4(rb.x - ob.x, rb.y - ob.y, rb.z - ob.z, rb.w - ob.w);
-    const float A = m0 + m3, B = m0 + m5;
-    const float Cc = A + m5;
-    const float D = Cc + m4, E = Cc - m4;
+    const float a1 = ra.x - oa.x, a2 = ra.y - oa.y, a3 = ra.z - oa.z, a4 = ra.w - oa.w;
+    const float a5 = rb.x - ob.x, a6 = rb.y - ob.y, a7 = rb.z - ob.z, a8 = rb.w - ob.w;
     const float G = m1 + m2, Hh = m1 - m2;
-    acc[0] = fmaf(A - m1, a.x, acc[0]);
-    acc[1] = fmaf(B - m2, a.y, acc[1]);
-    acc[2] = fmaf(A + m1, a.z, acc[2]);
-    acc[3] = fmaf(B + m2, a.w, acc[3]);
-    acc[4] = fmaf(D - G, b.x, acc[4]);
-    acc[5] = fmaf(E + Hh, b.y, acc[5]);
-    acc[6] = fmaf(D + G, b.z, acc[6]);
-    acc[7] = fmaf(E - Hh, b.w, acc[7]);
+    acc[0] = fmaf(-m1, a1, fmaf(U, a1, acc[0]));
+    acc[1] = fmaf(-m2, a2, fmaf(V, a2, acc[1]));
+    acc[2] = fmaf(m1, a3, fmaf(U, a3, acc[2]));
+    acc[3] = fmaf(m2, a4, fmaf(V, a4, acc[3]));
+    acc[4] = fmaf(-G, a5, fmaf(W, a5, acc[4]));
+    acc[5] = fmaf(Hh, a6, fmaf(Wp, a6, acc[5]));
+    acc[6] = fmaf(G, a7, fmaf(W, a7, acc[6]));
+    acc[7] = fmaf(-Hh, a8, fmaf(Wp, a8, acc[7]));
 }
 
 template <int KQ>
@@ -135,9 +150,13 @@ __device__ __forceinline__ float wls_general(const Stencil& S, const float4* __r
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const float* mc = reinterpret_cast<const float*>(m);
+            float tcol[6], mm[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) tcol[a] = mc[4 * a + c];
+            unbasis(tcol, mm);
             float w = 0.f;
 #pragma unroll
-            for (int a = 0; a < 6; ++a) w = fmaf(pb[a], mc[4 * a + c], w);
+            for (int a = 0; a < 6; ++a) w = fmaf(pb[a], mm[a], w);
             acc = fmaf(w, pop(f8, ids[c], k_src) - own, acc);
         }
     }

@@ -260,6 +260,14 @@ __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __rest
 #pragma unroll
                 for (int a = 0; a < 6; ++a) c[f][a] += __shfl_xor_sync(grp, c[f][a], 1);
         }
+        // coefficients of the stored basis -> monomial basis
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            float tc[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) tc[a] = c[f][a];
+            unbasis(tc, c[f]);
+        }
     } else {
         int ids[9];
         lag_block(S, p, ids);
@@ -516,12 +524,14 @@ __global__ void __launch_bounds__(128) force_kernel(Stencil S, int model, int n_
                         const int4 id = S.idx[(size_t)q * S.n_pad + p];
                         const int ids[4] = {id.x, id.y, id.z, id.w};
                         for (int c = 0; c < 4; ++c) {
-                            float w = 0.f;
+                            float tcol[6], mm[6];
                             for (int aa = 0; aa < 6; ++aa) {
                                 const float4 m = S.M[(size_t)(aa * KQ + q) * S.n_pad + p];
-                                const float mc = c == 0 ? m.x : (c == 1 ? m.y : (c == 2 ? m.z : m.w));
-                                w = fmaf(pb[aa], mc, w);
+                                tcol[aa] = c == 0 ? m.x : (c == 1 ? m.y : (c == 2 ? m.z : m.w));
                             }
+                            unbasis(tcol, mm);
+                            float w = 0.f;
+                            for (int aa = 0; aa < 6; ++aa) w = fmaf(pb[aa], mm[aa], w);
                             const float4 v = ruv[ids[c]];
                             d[0] = fmaf(w, v.x, d[0]);
                             d[1] = fmaf(w, v.y, d[1]);
@@ -685,6 +695,16 @@ inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
         default: return cudaErrorInvalidValue;           \
     }
 
+// the tuned variants (4 and up) are instantiated for K = 12, 16, 24, 32 only
+#define MLBM_DISPATCH_KQ_MAIN(KQ, ...)                   \
+    switch (KQ) {                                        \
+        case 3: { constexpr int KQC = 3; __VA_ARGS__; } break; \
+        case 4: { constexpr int KQC = 4; __VA_ARGS__; } break; \
+        case 6: { constexpr int KQC = 6; __VA_ARGS__; } break; \
+        case 8: { constexpr int KQC = 8; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;           \
+    }
+
 // grid of exactly the resident blocks (occupancy API), at most one per tile
 template <class F>
 cudaError_t run_persistent(const void* fn, int tile_nodes, int n, cudaStream_t, F launch) {
@@ -711,9 +731,12 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
         case 1: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 2, 1><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         case 2: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 2, 3><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         case 3: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 2, 4><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
-        case 8: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
-        case 9: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 2); }))); break;
-        case 10: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 1>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 1><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        case 8: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        case 9: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 2); }))); break;
+        case 10: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 1>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 1><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        case 11: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 12: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 2>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 2><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        case 13: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 3>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -728,9 +751,12 @@ cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* ou
         case 1: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 2, 1><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, in, out, C))); break;
         case 2: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 2, 3><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, in, out, C))); break;
         case 3: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 2, 4><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, in, out, C))); break;
-        case 8: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
-        case 9: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, in, out, C, 2); }))); break;
-        case 10: MLBM_DISPATCH_KQ(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 1>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 1><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
+        case 8: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
+        case 9: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 2, 3>, 128, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 2, 3><<<g, block, 0, st>>>(S, in, out, C, 2); }))); break;
+        case 10: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 1>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 1><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
+        case 11: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
+        case 12: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 2>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 2><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
+        case 13: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 3>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 3><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -364,6 +364,13 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
                             c[f][a] += __shfl_xor_sync(quad, c[f][a], 8);
                             c[f][a] += __shfl_xor_sync(quad, c[f][a], 16);
                         }
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        float tc[6];
+#pragma unroll
+                        for (int a = 0; a < 6; ++a) tc[a] = c[f][a];
+                        unbasis(tc, c[f]);
+                    }
                 } else {
                     const int4 i0 = sI[t], i1 = sI[TN + t], i2 = sI[2 * TN + t];
                     const int ids[9] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w, i2.x};

@@ -86,6 +86,7 @@ def lib():
                 "mlbm_set_kernel_variant": (st, [_vp, _i32]),
                 "mlbm_kernel_variant": (_i32, [_vp]),
                 "mlbm_autotune": (st, [_vp, _i32, _vp]),
+                "mlbm_autotune_ex": (st, [_vp, _i32, _i32, _vp]),
                 "mlbm_reduce_scratch_doubles": (_i64, [_i64]),
                 "mlbm_reduce_fields_device": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
                 "mlbm_last_error": (ctypes.c_char_p, []),
@@ -291,10 +292,10 @@ def kernel_variant(ctx: Context) -> int:
     return int(lib().mlbm_kernel_variant(ctx.handle))
 
 
-def autotune(ctx: Context, steps_per_variant: int = 20) -> tuple:
+def autotune(ctx: Context, steps_per_variant: int = 20, flush_l2: bool = False) -> tuple:
     """Pick the fastest kernel variant on this context; returns (variant, ms/step)."""
     ms = ctypes.c_double()
-    _check(lib().mlbm_autotune(ctx.handle, int(steps_per_variant), ctypes.byref(ms)))
+    _check(lib().mlbm_autotune_ex(ctx.handle, int(steps_per_variant), int(bool(flush_l2)), ctypes.byref(ms)))
     return kernel_variant(ctx), ms.value
 
 

@@ -48,7 +48,7 @@ def gpu_ctx(w, K, s, bb_mode, params, sigma=0.7071067811865476, use_lagrange=Tru
     return ctx
 
 
-VARIANTS = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10]
+VARIANTS = list(range(14))
 
 
 # ----------------------------------------------------------------- plain MLBM
@@ -327,6 +327,6 @@ def test_autotune_keeps_state_and_picks_a_variant():
     mlbm.step(ctx, 5)
     before = mlbm.get_fields(ctx)
     v, ms = mlbm.autotune(ctx, 5)
-    assert 0 <= v <= 10 and ms > 0
+    assert 0 <= v <= 13 and ms > 0
     assert mlbm.step_count(ctx) == 5
     assert np.array_equal(mlbm.get_fields(ctx), before)
