@@ -280,6 +280,28 @@ mlbm_status mlbm_reduce_fields_device(const float* rho, const float* ux, const f
                                       const uint8_t* mask, int64_t n, double* scratch, int64_t scratch_len,
                                       double* out, void* stream);
 
+/*
+ * mlbm_reduce_fields_device without a scratch argument, for callers that
+ * cannot allocate device memory: code that must run inside a memory budget
+ * fixed up front, code embedded in another runtime that owns the device pool,
+ * or latency-critical loops that cannot afford an allocation's implicit
+ * synchronisation.  The paper has no counterpart; this is a library service.
+ * The partial sums live in a file-scope device array of 6 * 1024 doubles
+ * (48 KiB) that every GPU loading the library keeps until exit; the
+ * reduction never needs more, for any n.  n must be in
+ * [0, mlbm_reduce_noalloc_max_nodes()] (2^31 - 1), else MLBM_E_INVALID.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (different streams, no ordering between them) race and give
+ * wrong sums.  Nothing in it has to start at zero (each call writes every
+ * partial it reads).  Calls no allocating routine.  Inputs and out[6] as for
+ * mlbm_reduce_fields_device.
+ */
+int64_t mlbm_reduce_noalloc_max_nodes(void);
+mlbm_status mlbm_reduce_fields_device_noalloc(const float* rho, const float* ux, const float* uy, const float* area,
+                                              const uint8_t* mask, int64_t n, double* out, void* stream);
+
 /* Last error message of this thread ("" when none). */
 const char* mlbm_last_error(void);
 

@@ -812,7 +812,7 @@ cudaError_t launch_force(const dev::Stencil& S, int model, int n_link_nodes, con
 
 int reduce_blocks(int64_t n) {
     const int64_t b = (n + 4 * dev::kRedThreads - 1) / (4 * dev::kRedThreads);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1024));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, kReduceMaxBlocks));
 }
 
 cudaError_t launch_reduce_fields(const float* rho, const float* ux, const float* uy, const float* area,

@@ -31,6 +31,8 @@ int force_blocks(int n_link_nodes);
 cudaError_t launch_force(const dev::Stencil& S, int model, int n_link_nodes, const int* link_nodes,
                          const float* area_over_s2, const float4* f8, const float4* ruv, const dev::Collide& C,
                          double* partial, double* out, cudaStream_t st);
+// the FP64 reductions never use more than this many partial-sum blocks
+constexpr int kReduceMaxBlocks = 1024;
 int reduce_blocks(int64_t n);
 cudaError_t launch_reduce_fields(const float* rho, const float* ux, const float* uy, const float* area,
                                  const uint8_t* mask, int64_t n, double* partial, double* out, cudaStream_t st);

@@ -89,6 +89,8 @@ def lib():
                 "mlbm_autotune_ex": (st, [_vp, _i32, _i32, _vp]),
                 "mlbm_reduce_scratch_doubles": (_i64, [_i64]),
                 "mlbm_reduce_fields_device": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
+                "mlbm_reduce_noalloc_max_nodes": (_i64, []),
+                "mlbm_reduce_fields_device_noalloc": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
                 "mlbm_last_error": (ctypes.c_char_p, []),
                 "mlbm_version": (ctypes.c_char_p, []),
             }
@@ -310,3 +312,10 @@ def reduce_fields_device(rho_ptr, ux_ptr, uy_ptr, area_ptr, mask_ptr, n, scratch
                                            _vp(mask_ptr) if mask_ptr else None, int(n), _vp(scratch_ptr),
                                            int(scratch_len), _vp(out_ptr),
                                            _vp(stream_handle) if stream_handle else None))
+
+
+def reduce_fields_device_noalloc(rho_ptr, ux_ptr, uy_ptr, area_ptr, mask_ptr, n, out_ptr, stream_handle=None):
+    """As reduce_fields_device, with the library's own static scratch (no allocation)."""
+    _check(lib().mlbm_reduce_fields_device_noalloc(_vp(rho_ptr), _vp(ux_ptr), _vp(uy_ptr), _vp(area_ptr),
+                                                   _vp(mask_ptr) if mask_ptr else None, int(n), _vp(out_ptr),
+                                                   _vp(stream_handle) if stream_handle else None))
