@@ -1,14 +1,16 @@
-"""Benchmark of the fused MLBM step on the cylinder-channel workload.
+"""Benchmark of the fused MLBM step on the vortex-street configuration.
 
-Workload: the Karman vortex street case -- a channel 22D x 4.1D with a
-cylinder of diameter D = 40 node spacings, ~260k scattered Poisson-disk nodes
-refined near the cylinder (seed 2), K = 16 least-squares stencils, BGK in
-FP32, Re = 100 with streaming distance s = 1/2 node spacing (D = 80 lattice
-units, U0 = 0.05, tau = 0.62), simple bounce-back on the cylinder,
-equilibrium inflow/outflow/side nodes.
-One bench "step" = one MLBM time step over all nodes = one fused kernel
-launch.  L2 is flushed (a 512 MiB write) before every timed step, so each
-step reads its stencil data from HBM.
+Workload: the Karman vortex street configuration as a whole -- a channel
+22D x 4.1D around a cylinder of diameter D = 40 node spacings, ~260k
+scattered Poisson-disk nodes refined near the cylinder (seed 2), K = 16
+least-squares stencils, BGK in FP32, simple bounce-back on the cylinder,
+equilibrium inflow/outflow/side nodes -- run for its six (Re, s) cases
+Re in {100, 200} x streaming distance s in {1/2, 1/4, 1/8} node spacings
+(D = 80, 160, 320 lattice units, U0 = 0.05, tau = 3 U0 D / Re + 1/2), all six
+advanced together in one batched context (one fused launch per time step,
+replayed from captured CUDA graphs).  One bench "step" = one time step of all
+six runs = 6 x 259,887 node updates.  The working set (~780 MB) is larger
+than L2, so consecutive steps are timed back to back without a flush.
 
 Arms:
   default            the CUDA path through the C ABI (device-resident state)
@@ -34,11 +36,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mnode-updates/s (FP32, err vs FP64 stated); time-to-steady warm vs cold"
 UNIT = "Mnode-updates/s"
-WORKLOAD = {"workload": "karman_cylinder_channel", "nodes": None, "K": 16, "model": "BGK", "Re": 100,
-            "s": 0.5, "tau": 0.62, "D_spacings": 40, "D_lattice": 80, "seed": 2, "bounce_back": "simple",
-            "l2": "flushed before every timed step (512 MiB write)"}
-TAU, RE, U0, D, S_STREAM = 0.62, 100, 0.05, 40.0, 0.5
-PROFILE = os.path.join(ROOT, "profiles", "bgk_step_karman260k.md")
+U0, D = 0.05, 40.0
+CASES = [(re, s) for re in (100, 200) for s in (0.5, 0.25, 0.125)]
+
+
+def tau_of(re, s):
+    return 3.0 * U0 * (D / s) / re + 0.5
+
+
+WORKLOAD = {"workload": "karman_vortex_street_sweep", "runs": [{"Re": re, "s": s, "tau": round(tau_of(re, s), 4)}
+                                                               for re, s in CASES],
+            "nodes_per_run": None, "node_updates_per_step": None, "K": 16, "model": "BGK", "D_spacings": 40,
+            "U0": U0, "seed": 2, "bounce_back": "simple",
+            "l2": "working set ~780 MB > L2; steps timed back to back"}
+TAU, S_STREAM = tau_of(100, 0.5), 0.5
+PROFILE = os.path.join(ROOT, "profiles", "bgk_step_karman_sweep.md")
 
 
 def algorithmic_bytes(info, K):
@@ -58,9 +70,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
+def measured_traffic(variant):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when it was taken on a different kernel source."""
+    or None when it was taken on a different kernel source or variant."""
     try:
         txt = open(PROFILE).read()
     except OSError:
@@ -70,7 +82,7 @@ def measured_traffic():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_hash") != kernel_source_hash():
+    if vals.get("kernel_source_hash") != kernel_source_hash() or vals.get("kernel_variant") != str(variant):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -155,6 +167,7 @@ def run_reference(args, rank, world):
     t = np.sort(rng.choice(w.n, size=n_sample, replace=False))
     op = O.Operator(w, K=16, s=S_STREAM, bb_mode=0, targets=t).check()
     f = O.equilibrium(np.ones(w.n), 0.0, 0.0)
+    # one of the six runs (Re = 100, s = 1/2); the others cost the same per node
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         O.bgk_step(op, f, TAU)
@@ -164,14 +177,14 @@ def run_reference(args, rank, world):
     total = sum(per_step)
     value = n_sample * args.steps / total / 1e6
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    cfg = dict(WORKLOAD, nodes=w.n)
+    cfg = dict(WORKLOAD, nodes_per_run=w.n, node_updates_per_step=w.n * len(CASES))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{n_sample} random nodes of the {w.n}-node workload per step"},
+                         "sample": f"{n_sample} random nodes of the {w.n}-node vortex-street node set (Re=100, s=1/2) per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -186,43 +199,41 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = make_workload()
-    st = mlbm.build_stencils_for(w, K=16, s=S_STREAM, bb_mode=mlbm.BB_SIMPLE)
-    info = mlbm.stencils_info(st)
-    params = mlbm.Params(mlbm.MODEL_BGK, TAU, 0.0, 0.0, 0.0)
-    ctx = mlbm.init(st, params)
-    variant, tune_ms = mlbm.autotune(ctx, 20, flush_l2=True)
+    st_by_s = {s: mlbm.build_stencils_for(w, K=16, s=s, bb_mode=mlbm.BB_SIMPLE) for s in sorted({s for _, s in CASES})}
+    sts = [st_by_s[s] for _, s in CASES]
+    params = [mlbm.Params(mlbm.MODEL_BGK, tau_of(re, s), 0.0, 0.0, 0.0) for re, s in CASES]
+    infos = [mlbm.stencils_info(st) for st in sts]
+    ctx = mlbm.batch_init(sts, params)
+    variant, tune_ms = mlbm.autotune(ctx, 10)
     stream = torch.cuda.Stream()
     mlbm.set_stream(ctx, stream.cuda_stream)
-    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 512 MiB > L2
+    n = ctx.n
     with torch.cuda.stream(stream):
         mlbm.step(ctx, args.warmup)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local_rank) if rank == 0 else None
     time.sleep(0.3 if clocks else 0)
     with torch.cuda.stream(stream):
-        for e0, e1 in ev:
-            flush.zero_()
-            e0.record(stream)
-            mlbm.step(ctx, 1)
-            e1.record(stream)
+        e0.record(stream)
+        mlbm.step(ctx, args.steps)
+        e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_ms = float(sum(step_ms))
+    total_ms = float(e0.elapsed_time(e1))
     if dist:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    n = w.n
     value = n * args.steps * world / (total_ms / 1e3) / 1e6
 
     # end to end through the public API with host buffers: upload the state
-    # from pinned memory, advance, read the fields and the cylinder force back
+    # of all six runs from pinned memory, advance, read the fields and the
+    # per-run cylinder forces back
     e2e_steps = max(args.steps, 1)
     f_host = torch.empty((n, 9), dtype=torch.float64, pin_memory=True).numpy()
     f_host[:] = mlbm.get_populations(ctx)
@@ -232,7 +243,7 @@ def run_ours(args, rank, world, local_rank):
     mlbm.set_populations(ctx, f_host)
     mlbm.step(ctx, e2e_steps)
     r = mlbm.lib().mlbm_get_fields(ctx.handle, ru_host.ctypes.data)
-    fx, fy, cd, cl = mlbm.drag_lift(ctx, D, U0)
+    forces = mlbm.batch_drag_lift(ctx, D, U0)
     e2e_s = time.perf_counter() - t0
     assert r == 0
     e2e_value = n * e2e_steps * world / e2e_s / 1e6
@@ -240,13 +251,15 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     pk, pk_kind = peaks()
-    bytes_launch = algorithmic_bytes(info, 16)
+    bytes_launch = sum(algorithmic_bytes(i, 16) for i in infos)
     avg_ms = total_ms / args.steps
     achieved = bytes_launch / (avg_ms / 1e3) / 1e9
-    traffic = measured_traffic()
+    traffic = measured_traffic(variant)
     cpu_val, cpu_threads, cpu_desc = oracle_sample_rate(w, 8192, 1, 10.0, 20000)
-    cfg = dict(WORKLOAD, nodes=n, parallelism=f"replicas x{world}", n_wls=info["n_wls"], n_eq=info["n_eq"],
-               n_links=info["n_links"], kernel_variant=variant, autotune_ms_per_step=tune_ms)
+    cfg = dict(WORKLOAD, nodes_per_run=w.n, node_updates_per_step=n, parallelism=f"replicas x{world}",
+               n_wls=int(sum(i["n_wls"] for i in infos)), n_eq=int(sum(i["n_eq"] for i in infos)),
+               n_links=int(sum(i["n_links"] for i in infos)), kernel_variant=variant,
+               autotune_ms_per_step=tune_ms, cuda_graph_chunk=16)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak",
@@ -256,11 +269,11 @@ def run_ours(args, rank, world, local_rank):
                      "note": f"algorithmic bytes {bytes_launch} per launch; peak {pk_kind} (burst copy)"},
         "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cpu_threads, "kind": "oracle", "sample": cpu_desc},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 9 * 8 / e2e_steps,
-                "d2h_bytes_per_step": (n * 3 * 8 + 16) / e2e_steps,
-                "note": f"set_populations from pinned host memory + {e2e_steps} steps + get_fields + drag_lift"},
+                "d2h_bytes_per_step": (n * 3 * 8 + 4 * 8 * len(CASES)) / e2e_steps,
+                "note": f"set_populations from pinned host memory + {e2e_steps} steps + get_fields + batch_drag_lift"},
         "gpu_launches": args.steps,
         "clocks": clk,
-        "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
+        "cd_after_e2e": [round(float(v), 4) for v in forces["cd"]],
     }
     print(json.dumps(out))
 

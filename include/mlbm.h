@@ -249,6 +249,12 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        ahead; 10 = one lane per node, one round ahead
  *   11   one lane per node, registers capped for 2 resident blocks of 256
  *   12-13 as 10 with registers capped for 2 / 3 resident blocks of 256
+ *   14-17 two lanes per node split by direction half (each lane gathers the
+ *        16-byte half record of its four directions): 14 = registers capped for
+ *        3 resident blocks of 256, all neighbour groups unrolled; 15 = capped
+ *        for 4 blocks, one group at a time; 16 = as 15, persistent with L2
+ *        prefetch; 17 = capped for 4 blocks, two groups at a time (BGK only;
+ *        the tau = 1 model runs variant 11 for these numbers)
  * Variants 4 and up are available for K = 12, 16, 24 and 32.
  * The default is 4 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream
@@ -262,6 +268,41 @@ mlbm_status mlbm_autotune(mlbm_ctx* ctx, int steps_per_variant, double* best_ms)
    512 MiB device write (a temporary buffer) so that steps are timed with a
    cold L2, and each step is timed on its own. */
 mlbm_status mlbm_autotune_ex(mlbm_ctx* ctx, int steps_per_variant, int flush_l2, double* best_ms);
+
+/* ------------------------------------------------------------------ batches */
+/*
+ * One context over several independent samples (node sets), advanced by the
+ * same fused launches: the samples' stencils are concatenated (sample i owns
+ * nodes [first_i, first_i + count_i) of the context, in the caller's order of
+ * that sample), each node knows its sample, and each sample has its own
+ * collision parameters (tau, tau_minus, body force); the streaming distance s
+ * is the one its stencils were built with.  All samples must share K, the
+ * bounce-back rule and the model.  Every single-context call works on the
+ * whole concatenation; the calls below give per-sample results.  Initial
+ * state: rest equilibrium (rho = 1, u = 0).
+ */
+mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* stencils, const mlbm_params* params,
+                            int n_samples);
+/* number of samples (1 for a context made by mlbm_init) */
+int mlbm_batch_size(const mlbm_ctx* ctx);
+mlbm_status mlbm_batch_range(const mlbm_ctx* ctx, int sample, int64_t* first, int64_t* count);
+/* mlbm_permeability per sample: arrays of mlbm_batch_size(ctx) entries (any may be NULL) */
+mlbm_status mlbm_batch_permeability(mlbm_ctx* ctx, double* k, double* u_superficial, double* u_intrinsic,
+                                    double* tortuosity);
+/* mlbm_drag_lift per sample: ref_length[i], u_ref[i] inputs, outputs of
+   mlbm_batch_size(ctx) entries (any may be NULL; NULL references give 0 coefficients) */
+mlbm_status mlbm_batch_drag_lift(mlbm_ctx* ctx, const double* ref_length, const double* u_ref, double* fx, double* fy,
+                                 double* cd, double* cl);
+/* mlbm_run_to_steady with the criterion per sample; all samples keep stepping
+   until every one has converged or max_steps is reached; steps_taken[i] is the
+   step count at which sample i converged (-1: not converged) */
+mlbm_status mlbm_batch_run_to_steady(mlbm_ctx* ctx, double tol, int64_t window, int64_t max_steps,
+                                     int64_t* steps_taken);
+
+/* mlbm_step replays chunks of 16 launches from captured CUDA graphs (one per
+   starting buffer, re-captured when the variant or stream changes); enable = 0
+   launches every step directly. */
+mlbm_status mlbm_set_graphs(mlbm_ctx* ctx, int enable);
 
 /* ------------------------------------------------ device-level reductions */
 /*

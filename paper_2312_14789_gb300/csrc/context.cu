@@ -65,7 +65,22 @@ struct mlbm_ctx {
     dev::Stencil S{};
     dev::Collide C{};
     std::vector<void*> allocations;
+    // batch of independent samples (empty for a single sample)
+    std::vector<int64_t> seg_off;  // position offset of each sample, plus the total
+    std::vector<mlbm_params> seg_params;
+    std::vector<double> seg_box_area;
+    std::vector<double> seg_s;  // streaming distance of each sample
+    double* seg_out = nullptr;  // device, 6 doubles per sample
+    // captured step graphs: chunk of kGraphSteps steps starting from buffer 0 / 1
+    bool use_graphs = true;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_variant = -1;
+    cudaStream_t graph_stream = nullptr;
 };
+
+namespace {
+constexpr int kGraphSteps = 16;
+}
 
 namespace {
 
@@ -178,7 +193,8 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
         hmask[q] = kind != kKindEq;
         hperm[q] = (int)H.perm[q];
         harea[q] = (float)H.area[q];
-        has2[q] = (float)(H.area[q] / (H.s * H.s));
+        const double sq = H.s_node.empty() ? H.s : H.s_node[q];
+        has2[q] = (float)(H.area[q] / (sq * sq));
         if (kind == kKindWls) {
             // stencil slots in increasing node position: lanes of a warp that
             // gather slot j of consecutive (Hilbert-ordered) nodes then touch
@@ -203,7 +219,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
                 const int j = H.lag_slot[(size_t)q * 9 + b];
                 hidx[(((size_t)(b / 4)) * np + q) * 4 + (b % 4)] = H.idx[(size_t)q * K + j];
             }
-            hlag[q] = (float)(H.s / H.lag_h[q]);
+            hlag[q] = (float)(sq / H.lag_h[q]);
         } else {
             heqv[q] = make_float4((float)(H.eqv[q * 3] - 1.0), (float)H.eqv[q * 3 + 1], (float)H.eqv[q * 3 + 2], 0.f);
         }
@@ -247,6 +263,12 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     c->scratch_len = std::max<int64_t>(6 * reduce_blocks(np), 2 * force_blocks(c->n_link_nodes));
     MLBM_TRY(dalloc(c, &c->scratch, c->scratch_len));
     MLBM_TRY(dalloc(c, &c->small, 16));
+    if (c->seg_off.empty()) {
+        c->seg_off = {0, n};
+        c->seg_params = {*p};
+        c->seg_box_area = {H.box_area};
+    }
+    MLBM_TRY(dalloc(c, &c->seg_out, 6 * (c->seg_off.size() - 1)));
     MLBM_TRY(dalloc(c, &c->err, 1));
     MLBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
     if (!tma_supported(Kq)) c->variant = 1;
@@ -302,9 +324,19 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     return sync(c);
 }
 
+void drop_graphs(mlbm_ctx* c) {
+    for (int i = 0; i < 2; ++i)
+        if (c->graph[i]) {
+            cudaGraphExecDestroy(c->graph[i]);
+            c->graph[i] = nullptr;
+        }
+    c->graph_variant = -1;
+}
+
 void free_ctx(mlbm_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
     for (void* p : c->allocations) cudaFree(p);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -315,8 +347,8 @@ void free_ctx(mlbm_ctx* c) {
 mlbm_status fields_to_work(mlbm_ctx* c, double* ru_dev_or_null) {
     const int n = (int)c->n;
     MLBM_CUDA(launch_macroscopics(c->params.model, n, c->perm, c->f8[c->cur], c->f0[c->cur], c->ruv[c->cur],
-                                  (float)c->params.gx, (float)c->params.gy, c->rho, c->ux, c->uy, ru_dev_or_null,
-                                  c->stream));
+                                  (float)c->params.gx, (float)c->params.gy, c->S.node_sample, c->S.coll, c->rho,
+                                  c->ux, c->uy, ru_dev_or_null, c->stream));
     return MLBM_OK;
 }
 
@@ -402,7 +434,39 @@ mlbm_status mlbm_step(mlbm_ctx* c, int64_t n_steps) {
     if (n_steps < 0) return set_error(MLBM_E_INVALID, "step: negative step count");
     if (n_steps == 0) return MLBM_OK;
     if (c->timing) MLBM_CUDA(cudaEventRecord(c->ev0, c->stream));
-    for (int64_t t = 0; t < n_steps; ++t) MLBM_TRY(launch_one_step(c, c->variant));
+    int64_t left = n_steps;
+    if (c->use_graphs && n_steps >= kGraphSteps) {
+        if (c->graph_variant != c->variant || c->graph_stream != c->stream) {
+            drop_graphs(c);
+            c->graph_variant = c->variant;
+            c->graph_stream = c->stream;
+        }
+        while (left >= kGraphSteps) {
+            cudaGraphExec_t& ex = c->graph[c->cur];
+            if (!ex) {
+                // capture kGraphSteps launches; cur returns to its value (even count)
+                cudaGraph_t g = nullptr;
+                MLBM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                mlbm_status cs = MLBM_OK;
+                for (int i = 0; i < kGraphSteps && cs == MLBM_OK; ++i) cs = launch_one_step(c, c->variant);
+                cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+                if (cs != MLBM_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return cs;
+                }
+                if (ee != cudaSuccess) return set_error(MLBM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+                ee = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                if (ee != cudaSuccess) {
+                    ex = nullptr;
+                    return set_error(MLBM_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
+                }
+            }
+            MLBM_CUDA(cudaGraphLaunch(ex, c->stream));
+            left -= kGraphSteps;
+        }
+    }
+    for (int64_t t = 0; t < left; ++t) MLBM_TRY(launch_one_step(c, c->variant));
     c->steps += n_steps;
     if (c->timing) {
         MLBM_CUDA(cudaEventRecord(c->ev1, c->stream));
@@ -553,7 +617,7 @@ mlbm_status mlbm_load(mlbm_ctx* c, const char* path) {
 
 mlbm_status mlbm_set_kernel_variant(mlbm_ctx* c, int variant) {
     if (!c) return set_error(MLBM_E_INVALID, "set_kernel_variant: NULL context");
-    if (variant < 0 || variant > 13 || (variant >= 4 && !tma_supported(c->K / 4)))
+    if (variant < 0 || variant > 17 || (variant >= 4 && !tma_supported(c->K / 4)))
         return set_error(MLBM_E_INVALID, "set_kernel_variant: variant not available for this K");
     c->variant = variant;
     return MLBM_OK;
@@ -604,7 +668,8 @@ mlbm_status mlbm_autotune_ex(mlbm_ctx* c, int steps_per_variant, int flush_l2, d
     }
     int best = c->variant;
     double best_t = 1e30;
-    for (int v = 0; v <= 13 && st == MLBM_OK; ++v) {
+    for (int v = 0; v <= 17 && st == MLBM_OK; ++v) {
+        if (v >= 14 && c->params.model != MLBM_MODEL_BGK) continue;
         if (v >= 4 && !tma_supported(c->K / 4)) continue;
         // one untimed warm-up launch, then the timed ones
         st = launch_one_step(c, v);
@@ -668,6 +733,240 @@ mlbm_status mlbm_autotune_ex(mlbm_ctx* c, int steps_per_variant, int flush_l2, d
     if (st != MLBM_OK) return st;
     c->variant = best;
     if (best_ms) *best_ms = best_t;
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, const mlbm_params* params,
+                            int n_samples) {
+    clear_error();
+    if (!out || !sts || !params || n_samples < 1 || n_samples > 65535)
+        return set_error(MLBM_E_INVALID, "batch_init: bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < n_samples; ++i) {
+        if (!sts[i]) return set_error(MLBM_E_INVALID, "batch_init: NULL stencils");
+        MLBM_TRY(check_params(&params[i]));
+        if (sts[i]->h.K != sts[0]->h.K || sts[i]->h.bb_mode != sts[0]->h.bb_mode ||
+            params[i].model != params[0].model)
+            return set_error(MLBM_E_INVALID, "batch_init: samples must share K, bounce-back rule and model");
+    }
+    // concatenate the samples' host stencils; sample i keeps its own Hilbert
+    // order inside positions [off_i, off_i + n_i)
+    auto* cat = new (std::nothrow) mlbm_stencils;
+    if (!cat) return set_error(MLBM_E_OOM, "batch_init: out of host memory");
+    HostStencils& C = cat->h;
+    const int K = sts[0]->h.K;
+    C.K = K;
+    C.s = sts[0]->h.s;
+    C.bb_mode = sts[0]->h.bb_mode;
+    std::vector<int64_t> off(n_samples + 1, 0);
+    for (int i = 0; i < n_samples; ++i) off[i + 1] = off[i] + sts[i]->h.n;
+    const int64_t n = off[n_samples];
+    if (n > (int64_t(1) << 31) - 1) {
+        delete cat;
+        return set_error(MLBM_E_INVALID, "batch_init: more than 2^31 - 1 nodes in total");
+    }
+    C.n = n;
+    C.box_area = 0;
+    C.perm.resize(n); C.inv.resize(n); C.idx.resize((size_t)n * K); C.M.resize((size_t)n * 6 * K);
+    C.kind.resize(n); C.center.resize(n); C.lag_h.resize(n); C.lag_slot.resize((size_t)n * 9);
+    C.link_mask.resize(n); C.q.resize((size_t)n * 9); C.eqv.resize((size_t)n * 3); C.area.resize(n);
+    C.s_node.resize(n);
+    std::vector<uint16_t> node_sample(n);
+    for (int i = 0; i < n_samples; ++i) {
+        const HostStencils& H = sts[i]->h;
+        const int64_t o = off[i];
+        for (int64_t p = 0; p < H.n; ++p) {
+            C.perm[o + p] = o + H.perm[p];
+            C.inv[o + H.perm[p]] = o + p;
+            for (int j = 0; j < K; ++j) C.idx[(size_t)(o + p) * K + j] = (int32_t)(o + H.idx[(size_t)p * K + j]);
+            C.s_node[o + p] = H.s;
+            node_sample[o + p] = (uint16_t)i;
+        }
+        std::copy(H.M.begin(), H.M.end(), C.M.begin() + (size_t)o * 6 * K);
+        std::copy(H.kind.begin(), H.kind.end(), C.kind.begin() + o);
+        std::copy(H.center.begin(), H.center.end(), C.center.begin() + o);
+        std::copy(H.lag_h.begin(), H.lag_h.end(), C.lag_h.begin() + o);
+        std::copy(H.lag_slot.begin(), H.lag_slot.end(), C.lag_slot.begin() + (size_t)o * 9);
+        std::copy(H.link_mask.begin(), H.link_mask.end(), C.link_mask.begin() + o);
+        std::copy(H.q.begin(), H.q.end(), C.q.begin() + (size_t)o * 9);
+        std::copy(H.eqv.begin(), H.eqv.end(), C.eqv.begin() + (size_t)o * 3);
+        std::copy(H.area.begin(), H.area.end(), C.area.begin() + o);
+        C.info.n_wls += H.info.n_wls;
+        C.info.n_lagrange += H.info.n_lagrange;
+        C.info.n_eq += H.info.n_eq;
+        C.info.n_link_nodes += H.info.n_link_nodes;
+        C.info.n_links += H.info.n_links;
+    }
+    C.info.n = n;
+    C.info.K = K;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        (void)cudaGetLastError();
+        delete cat;
+        return set_error(MLBM_E_CUDA, "batch_init: no CUDA device");
+    }
+    auto* c = new (std::nothrow) mlbm_ctx;
+    if (!c) {
+        delete cat;
+        return set_error(MLBM_E_OOM, "batch_init: out of host memory");
+    }
+    c->seg_off = off;
+    c->seg_params.assign(params, params + n_samples);
+    for (int i = 0; i < n_samples; ++i) {
+        c->seg_box_area.push_back(sts[i]->h.box_area);
+        c->seg_s.push_back(sts[i]->h.s);
+    }
+    mlbm_status st = do_init(c, cat, &params[0], nullptr, nullptr);
+    delete cat;
+    if (st == MLBM_OK) {
+        // per-sample collision table and per-node sample index
+        std::vector<dev::Collide> table(n_samples);
+        for (int i = 0; i < n_samples; ++i) {
+            mlbm_ctx tmp;
+            tmp.params = params[i];
+            set_collide(&tmp);
+            table[i] = tmp.C;
+        }
+        uint16_t* d_ns = nullptr;
+        dev::Collide* d_coll = nullptr;
+        st = dalloc(c, &d_ns, (size_t)c->n_pad);
+        if (st == MLBM_OK) st = dalloc(c, &d_coll, (size_t)n_samples);
+        if (st == MLBM_OK) st = upload(c, d_ns, node_sample.data(), (size_t)n * 2);
+        if (st == MLBM_OK) st = upload(c, d_coll, table.data(), table.size() * sizeof(dev::Collide));
+        if (st == MLBM_OK) {
+            c->S.node_sample = d_ns;
+            c->S.coll = d_coll;
+            st = sync(c);
+        }
+    }
+    if (st != MLBM_OK) {
+        std::string msg = g_last_error;
+        free_ctx(c);
+        return set_error(st, msg);
+    }
+    *out = c;
+    return MLBM_OK;
+}
+
+int mlbm_batch_size(const mlbm_ctx* c) { return c ? (int)c->seg_off.size() - 1 : -1; }
+
+mlbm_status mlbm_batch_range(const mlbm_ctx* c, int sample, int64_t* first, int64_t* count) {
+    if (!c || sample < 0 || sample >= (int)c->seg_off.size() - 1) return set_error(MLBM_E_INVALID, "batch_range: bad sample");
+    if (first) *first = c->seg_off[sample];
+    if (count) *count = c->seg_off[sample + 1] - c->seg_off[sample];
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_batch_permeability(mlbm_ctx* c, double* k, double* us, double* ui, double* tort) {
+    if (!c) return set_error(MLBM_E_INVALID, "batch_permeability: NULL context");
+    const int ns = (int)c->seg_off.size() - 1;
+    MLBM_TRY(fields_to_work(c, nullptr));
+    for (int i = 0; i < ns; ++i) {
+        const int64_t o = c->seg_off[i], m = c->seg_off[i + 1] - o;
+        MLBM_CUDA(launch_reduce_fields(c->rho + o, c->ux + o, c->uy + o, c->area + o, c->mask + o, m, c->scratch,
+                                       c->seg_out + 6 * i, c->stream));
+    }
+    std::vector<double> h(6 * (size_t)ns);
+    MLBM_CUDA(cudaMemcpyAsync(h.data(), c->seg_out, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    MLBM_TRY(sync(c));
+    for (int i = 0; i < ns; ++i) {
+        const double* v = &h[6 * (size_t)i];
+        const mlbm_params& p = c->seg_params[i];
+        const double sup = v[2] / c->seg_box_area[i];
+        const double gmag = std::sqrt(p.gx * p.gx + p.gy * p.gy);
+        const double nu = (p.tau - 0.5) / 3.0;
+        if (us) us[i] = sup;
+        if (ui) ui[i] = v[0] != 0 ? v[2] / v[0] : 0.0;
+        if (k) k[i] = gmag > 0 ? nu * sup / gmag : 0.0;
+        if (tort) tort[i] = v[2] != 0 ? v[4] / v[2] : 0.0;
+    }
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_batch_run_to_steady(mlbm_ctx* c, double tol, int64_t window, int64_t max_steps, int64_t* taken) {
+    if (!c) return set_error(MLBM_E_INVALID, "batch_run_to_steady: NULL context");
+    if (!(tol > 0) || window < 1 || max_steps < 0) return set_error(MLBM_E_INVALID, "batch_run_to_steady: bad arguments");
+    const int ns = (int)c->seg_off.size() - 1;
+    std::vector<int64_t> at(ns, -1);
+    auto snapshot = [&](double* host) -> mlbm_status {
+        MLBM_TRY(fields_to_work(c, nullptr));
+        for (int i = 0; i < ns; ++i) {
+            const int64_t o = c->seg_off[i], m = c->seg_off[i + 1] - o;
+            MLBM_CUDA(launch_change(c->ux + o, c->uy + o, c->px + o, c->py + o, c->mask + o, m, c->scratch,
+                                    c->seg_out + 2 * i, c->stream));
+        }
+        if (host) MLBM_CUDA(cudaMemcpyAsync(host, c->seg_out, 16 * (size_t)ns, cudaMemcpyDeviceToHost, c->stream));
+        return sync(c);
+    };
+    MLBM_TRY(snapshot(nullptr));
+    int64_t done = 0;
+    int remaining = ns;
+    std::vector<double> h(2 * (size_t)ns);
+    while (done < max_steps && remaining > 0) {
+        const int64_t w = std::min(window, max_steps - done);
+        MLBM_TRY(mlbm_step(c, w));
+        done += w;
+        MLBM_TRY(snapshot(h.data()));
+        for (int i = 0; i < ns; ++i) {
+            if (at[i] >= 0) continue;
+            if (!std::isfinite(h[2 * i]) || !std::isfinite(h[2 * i + 1]))
+                return set_error(MLBM_E_DIVERGED, "batch_run_to_steady: non-finite velocity in sample " + std::to_string(i));
+            const double delta = h[2 * i + 1] > 0 ? std::sqrt(h[2 * i] / h[2 * i + 1]) / (double)w : 0.0;
+            if (w == window && delta < tol) {
+                at[i] = done;
+                --remaining;
+            }
+        }
+    }
+    if (taken)
+        for (int i = 0; i < ns; ++i) taken[i] = at[i];
+    return remaining == 0 ? MLBM_OK : set_error(MLBM_E_NOT_CONVERGED, "batch_run_to_steady: max_steps reached");
+}
+
+mlbm_status mlbm_batch_drag_lift(mlbm_ctx* c, const double* ref_length, const double* u_ref, double* fx, double* fy,
+                                 double* cd, double* cl) {
+    if (!c) return set_error(MLBM_E_INVALID, "batch_drag_lift: NULL context");
+    const int ns = (int)c->seg_off.size() - 1;
+    // link nodes are listed in position order and samples own contiguous
+    // position ranges, so each sample's links are a contiguous slice
+    std::vector<int> lo(ns + 1, 0);
+    {
+        std::vector<int> hl(c->n_link_nodes);
+        if (c->n_link_nodes)
+            MLBM_CUDA(cudaMemcpyAsync(hl.data(), c->link_nodes, hl.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+        MLBM_TRY(sync(c));
+        for (int i = 0; i <= ns; ++i)
+            lo[i] = (int)(std::lower_bound(hl.begin(), hl.end(), (int)c->seg_off[i]) - hl.begin());
+    }
+    std::vector<double> h(2 * (size_t)ns, 0.0);
+    for (int i = 0; i < ns; ++i) {
+        const int m = lo[i + 1] - lo[i];
+        if (m == 0) continue;
+        MLBM_CUDA(launch_force(c->S, c->params.model, m, c->link_nodes + lo[i], c->area_over_s2, c->f8[c->cur],
+                               c->ruv[c->cur], c->C, c->scratch, c->seg_out + 2 * i, c->stream));
+    }
+    std::vector<double> dv(2 * (size_t)ns);
+    MLBM_CUDA(cudaMemcpyAsync(dv.data(), c->seg_out, dv.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    MLBM_TRY(sync(c));
+    for (int i = 0; i < ns; ++i) {
+        const bool any = lo[i + 1] > lo[i];
+        const double Fx = any ? dv[2 * i] : 0.0, Fy = any ? dv[2 * i + 1] : 0.0;
+        if (fx) fx[i] = Fx;
+        if (fy) fy[i] = Fy;
+        const double sq = c->seg_s.empty() ? c->s : c->seg_s[i];
+        const double L = ref_length ? ref_length[i] / sq : 0.0;
+        const double u = u_ref ? u_ref[i] : 0.0;
+        const double den = u * u * L;
+        if (cd) cd[i] = den != 0 ? 2.0 * Fx / den : 0.0;
+        if (cl) cl[i] = den != 0 ? 2.0 * Fy / den : 0.0;
+    }
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_set_graphs(mlbm_ctx* c, int enable) {
+    if (!c) return set_error(MLBM_E_INVALID, "set_graphs: NULL context");
+    c->use_graphs = enable != 0;
+    if (!c->use_graphs) drop_graphs(c);
     return MLBM_OK;
 }
 

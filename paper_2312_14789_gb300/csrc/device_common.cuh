@@ -29,6 +29,12 @@ struct LinkRec {
     float t[8];     // departure factor 1 - 2q of direction k at t[k-1]
 };
 
+struct Collide {
+    float omega_p, omega_m;  // 1/tau+, 1/tau-
+    float src_p, src_m;      // 1 - 1/(2 tau+), 1 - 1/(2 tau-)
+    float ax, ay;            // body acceleration
+};
+
 struct Stencil {
     int n, n_pad, K, Kq;
     int bb_mode;
@@ -39,13 +45,16 @@ struct Stencil {
     const int* link_slot;
     const LinkRec* links;
     const float4* eqv;
+    // batches of independent samples: sample of each node and the collision
+    // parameters of each sample (both null for a single sample)
+    const uint16_t* node_sample;
+    const Collide* coll;
 };
 
-struct Collide {
-    float omega_p, omega_m;  // 1/tau+, 1/tau-
-    float src_p, src_m;      // 1 - 1/(2 tau+), 1 - 1/(2 tau-)
-    float ax, ay;            // body acceleration
-};
+// collision parameters of node p
+__device__ __forceinline__ Collide collide_of(const Stencil& S, const Collide& C0, int p) {
+    return S.node_sample ? S.coll[S.node_sample[p]] : C0;
+}
 
 __device__ __forceinline__ int ex_of(int k) { return (k == 1 || k == 5 || k == 8) ? 1 : ((k == 3 || k == 6 || k == 7) ? -1 : 0); }
 __device__ __forceinline__ int ey_of(int k) { return (k == 2 || k == 5 || k == 6) ? 1 : ((k == 4 || k == 7 || k == 8) ? -1 : 0); }

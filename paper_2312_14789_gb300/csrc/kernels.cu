@@ -32,7 +32,8 @@ namespace dev {
 template <int KQ, int LPN>
 __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restrict__ f8in,
                                          const float* __restrict__ f0in, float4* __restrict__ f8out,
-                                         float* __restrict__ f0out, const Collide& C, int p, int h, unsigned grp) {
+                                         float* __restrict__ f0out, const Collide& C0, int p, int h, unsigned grp) {
+    const Collide C = collide_of(S, C0, p);
     const uint8_t meta = S.meta[p];
     const int kind = meta & 3;
     float g[9];
@@ -140,6 +141,149 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
     if (LPN == 1 || h == 1) f8out[2 * (size_t)p + 1] = make_float4(g[5], g[6], g[7], g[8]);
 }
 
+// Two lanes per node split by direction half: lane h gathers only the
+// 16-byte half record f_{4h+1..4h+4} of each stencil node (one load per
+// neighbour) and needs only four of the six matrix rows; every direction's
+// opposite lies in the same half, so bounce-back stays in the lane.  The
+// halves are exchanged with four shuffles before the pair-split collision
+// (pairs (1,3), (2,4) on lane 0, (5,7), (6,8) on lane 1).
+template <int KQ, int UQ>
+__device__ __forceinline__ void bgk_node_split(const Stencil& S, const float4* __restrict__ f8in,
+                                               const float* __restrict__ f0in, float4* __restrict__ f8out,
+                                               float* __restrict__ f0out, const Collide& C0, int p, int h,
+                                               unsigned grp) {
+    const Collide C = collide_of(S, C0, p);
+    const uint8_t meta = S.meta[p];
+    const int kind = meta & 3;
+    float g[9];
+    if (kind == 2) {
+        const float4 e = S.eqv[p];
+        eq_populations(e.x, e.y, e.z, g);
+    } else {
+        const float4 own = __ldg(f8in + 2 * (size_t)p + h);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float r = (kind == 1) ? __ldg(S.lag_r + p) : 0.f;
+        const float cx = (kind == 1) ? (float)ex_of(meta >> 4) : 0.f;
+        const float cy = (kind == 1) ? (float)ey_of(meta >> 4) : 0.f;
+        if (kind == 0) {
+            const int ra = h ? 2 : 0, rb = h ? 3 : 1;
+            // UQ neighbour groups in flight at a time (register budget)
+#pragma unroll UQ
+            for (int q = 0; q < KQ; ++q) {
+                const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                const float4 mA = ld_stream(S.M + (size_t)(ra * KQ + q) * S.n_pad + p);
+                const float4 mB = ld_stream(S.M + (size_t)(rb * KQ + q) * S.n_pad + p);
+                const float4 m1 = ld_stream(S.M + (size_t)(4 * KQ + q) * S.n_pad + p);
+                const float4 m2 = ld_stream(S.M + (size_t)(5 * KQ + q) * S.n_pad + p);
+                const int ids[4] = {id.x, id.y, id.z, id.w};
+                const float A4[4] = {mA.x, mA.y, mA.z, mA.w}, B4[4] = {mB.x, mB.y, mB.z, mB.w};
+                const float P4[4] = {m1.x, m1.y, m1.z, m1.w}, Q4[4] = {m2.x, m2.y, m2.z, m2.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float4 v = __ldg(f8in + 2 * (size_t)ids[c] + h);
+                    const float a0 = v.x - own.x, a1 = v.y - own.y, a2 = v.z - own.z, a3 = v.w - own.w;
+                    // h = 0: A = U, B = V, X = m1, Y = m2 ; h = 1: A = W, B = W', X = m1 + m2, Y = m1 - m2
+                    const float X = h ? P4[c] + Q4[c] : P4[c];
+                    const float Y = h ? P4[c] - Q4[c] : Q4[c];
+                    // h = 0: k = 1 (A - X), 2 (B - Y), 3 (A + X), 4 (B + Y)
+                    // h = 1: k = 5 (A - X), 6 (B + Y), 7 (A + X), 8 (B - Y)
+                    const float sy = h ? 1.f : -1.f;
+                    acc[0] = fmaf(-X, a0, fmaf(A4[c], a0, acc[0]));
+                    acc[1] = fmaf(sy * Y, a1, fmaf(B4[c], a1, acc[1]));
+                    acc[2] = fmaf(X, a2, fmaf(A4[c], a2, acc[2]));
+                    acc[3] = fmaf(-sy * Y, a3, fmaf(B4[c], a3, acc[3]));
+                }
+            }
+        } else {
+            int ids[9];
+            lag_block(S, p, ids);
+            float xp[3], x0[3], xm[3], yp[3], y0[3], ym[3];
+            lag3(-r - cx, xp[0], xp[1], xp[2]);
+            lag3(-cx, x0[0], x0[1], x0[2]);
+            lag3(r - cx, xm[0], xm[1], xm[2]);
+            lag3(-r - cy, yp[0], yp[1], yp[2]);
+            lag3(-cy, y0[0], y0[1], y0[2]);
+            lag3(r - cy, ym[0], ym[1], ym[2]);
+#pragma unroll
+            for (int bp = 0; bp < 9; ++bp) {
+                const int b = bp / 3, a = bp % 3;
+                const float4 v = __ldg(f8in + 2 * (size_t)ids[bp] + h);
+                // weights of this half's four directions
+                const float w0 = h ? xp[a] * yp[b] : xp[a] * y0[b];
+                const float w1 = h ? xm[a] * yp[b] : x0[a] * yp[b];
+                const float w2 = h ? xm[a] * ym[b] : xm[a] * y0[b];
+                const float w3 = h ? xp[a] * ym[b] : x0[a] * ym[b];
+                acc[0] = fmaf(w0, v.x - own.x, acc[0]);
+                acc[1] = fmaf(w1, v.y - own.y, acc[1]);
+                acc[2] = fmaf(w2, v.z - own.z, acc[2]);
+                acc[3] = fmaf(w3, v.w - own.w, acc[3]);
+            }
+        }
+        acc[0] += own.x;
+        acc[1] += own.y;
+        acc[2] += own.z;
+        acc[3] += own.w;
+        if (meta & 4) {
+            const LinkRec L = S.links[S.link_slot[p]];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * h + i + 1;
+                if (!((L.mask >> k) & 1u)) continue;
+                const int kp = opp_of(k);
+                float v;
+                if (S.bb_mode == 0) {
+                    v = pop(f8in, p, kp);
+                } else if (kind == 0) {
+                    float pb[6];
+                    basis_at(k, L.t[k - 1], pb);
+                    v = wls_general<KQ>(S, f8in, p, kp, pb);
+                } else {
+                    int ids[9];
+                    lag_block(S, p, ids);
+                    const float tt = L.t[k - 1];
+                    float lx[3], ly[3];
+                    lag3(tt * r * ex_of(k) - cx, lx[0], lx[1], lx[2]);
+                    lag3(tt * r * ey_of(k) - cy, ly[0], ly[1], ly[2]);
+                    const float o = pop(f8in, p, kp);
+                    float sacc = 0.f;
+                    for (int b = 0; b < 3; ++b)
+                        for (int a = 0; a < 3; ++a) sacc = fmaf(lx[a] * ly[b], pop(f8in, ids[b * 3 + a], kp) - o, sacc);
+                    v = o + sacc;
+                }
+                acc[i] = v;
+            }
+        }
+        float oth[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) oth[i] = __shfl_xor_sync(grp, acc[i], 1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            g[1 + i] = h ? oth[i] : acc[i];
+            g[5 + i] = h ? acc[i] : oth[i];
+        }
+        g[0] = f0in[p];
+        collide_pairs(g, C, h == 0 ? 0x3u : 0xCu, h == 0);
+    }
+    if (h == 0) {
+        f8out[2 * (size_t)p] = make_float4(g[1], g[2], g[3], g[4]);
+        f0out[p] = g[0];
+    } else {
+        f8out[2 * (size_t)p + 1] = make_float4(g[5], g[6], g[7], g[8]);
+    }
+}
+
+template <int KQ, int MINB, int UQ>
+__global__ void __launch_bounds__(256, MINB) bgk_split_kernel(Stencil S, const float4* __restrict__ f8in,
+                                                              const float* __restrict__ f0in,
+                                                              float4* __restrict__ f8out, float* __restrict__ f0out,
+                                                              Collide C) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = tid >> 1;
+    if (p >= S.n) return;
+    const unsigned lane = threadIdx.x & 31u;
+    bgk_node_split<KQ, UQ>(S, f8in, f0in, f8out, f0out, C, p, tid & 1, 3u << (lane & ~1u));
+}
+
 // Bulk prefetch of a node tile's stencil rows (matrix, indices, meta) into L2,
 // issued by the lanes of one warp; no registers or shared memory are used.
 __device__ __forceinline__ void prefetch_l2(const void* ptr, uint32_t bytes) {
@@ -212,9 +356,27 @@ __device__ __forceinline__ void eval_coeffs(const float (*c)[6], const float* pb
 // LPN lanes per node: neighbour groups split as in the BGK kernel, the 18
 // fitted coefficients combined by a pair shuffle, the 8 directions split
 // (lane 0: k = 0..4, lane 1: k = 5..8) and the moment sums combined again.
+template <int KQ, int MINB, int UQ>
+__global__ void __launch_bounds__(256, MINB) bgk_split_persistent(Stencil S, const float4* __restrict__ f8in,
+                                                                  const float* __restrict__ f0in,
+                                                                  float4* __restrict__ f8out,
+                                                                  float* __restrict__ f0out, Collide C, int dist) {
+    constexpr int TN = 128;
+    const int n_tiles = (S.n + TN - 1) / TN;
+    const unsigned lane = threadIdx.x & 31u;
+    if (threadIdx.x < 32)
+        for (int d = 0; d < dist; ++d) prefetch_tile<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (threadIdx.x < 32) prefetch_tile<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
+        const int p = tile * TN + (threadIdx.x >> 1);
+        if (p < S.n) bgk_node_split<KQ, UQ>(S, f8in, f0in, f8out, f0out, C, p, threadIdx.x & 1, 3u << (lane & ~1u));
+    }
+}
+
 template <int KQ, int LPN>
 __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __restrict__ in, float4* __restrict__ out,
-                                          const Collide& C, int p, int h, unsigned grp) {
+                                          const Collide& C0, int p, int h, unsigned grp) {
+    const Collide C = collide_of(S, C0, p);
     const uint8_t meta = S.meta[p];
     const int kind = meta & 3;
     if (kind == 2) {
@@ -430,10 +592,14 @@ __global__ void get_tau1_to_f64(int n, const int* __restrict__ perm, const float
 // rho, u of the state into FP32 sorted-order arrays (and optionally FP64
 // caller-order rho_u[n][3]).  BGK: rho = sum f, rho u = sum f e - rho a / 2.
 __global__ void macroscopics_bgk(int n, const int* __restrict__ perm, const float4* __restrict__ f8,
-                                 const float* __restrict__ f0, float ax, float ay, float* __restrict__ rho_o,
-                                 float* __restrict__ ux_o, float* __restrict__ uy_o, double* __restrict__ ru) {
+                                 const float* __restrict__ f0, float ax0, float ay0,
+                                 const uint16_t* __restrict__ node_sample, const Collide* __restrict__ coll,
+                                 float* __restrict__ rho_o, float* __restrict__ ux_o, float* __restrict__ uy_o,
+                                 double* __restrict__ ru) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
+    const float ax = node_sample ? coll[node_sample[p]].ax : ax0;
+    const float ay = node_sample ? coll[node_sample[p]].ay : ay0;
     const float4 a = f8[2 * (size_t)p], b = f8[2 * (size_t)p + 1];
     const float g0 = f0[p];
     const float dr = g0 + (a.x + a.y + a.z + a.w) + (b.x + b.y + b.z + b.w);
@@ -483,6 +649,7 @@ __global__ void __launch_bounds__(128) force_kernel(Stencil S, int model, int n_
     double fx = 0.0, fy = 0.0;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_link_nodes; e += gridDim.x * blockDim.x) {
         const int p = link_nodes[e];
+        const Collide Cn = collide_of(S, C, p);
         const uint8_t meta = S.meta[p];
         const int kind = meta & 3;
         const LinkRec L = S.links[S.link_slot[p]];
@@ -555,7 +722,7 @@ __global__ void __launch_bounds__(128) force_kernel(Stencil S, int model, int n_
                         }
                 }
                 const float rd = 1.0f + d[0];
-                val = geq(kp, d[0], rd, d[1], d[2]) + 0.5f * src(kp, rd, d[1], d[2], C.ax, C.ay);
+                val = geq(kp, d[0], rd, d[1], d[2]) + 0.5f * src(kp, rd, d[1], d[2], Cn.ax, Cn.ay);
             }
             fx += 2.0 * (double)val * ex_of(kp) * a;
             fy += 2.0 * (double)val * ey_of(kp) * a;
@@ -737,6 +904,10 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
         case 11: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         case 12: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 2>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 2><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
         case 13: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 3>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        case 14: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_split_kernel<KQC, 3, KQC><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 15: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_split_kernel<KQC, 4, 1><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 16: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_split_persistent<KQC, 4, 1>, 128, S.n, st, [&](int g) { dev::bgk_split_persistent<KQC, 4, 1><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        case 17: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_split_kernel<KQC, 4, 2><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -757,6 +928,11 @@ cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* ou
         case 11: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
         case 12: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 2>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 2><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
         case 13: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 3>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 3><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
+        case 14:
+        case 15:
+        case 16:
+        case 17:  // the direction split exists for the populations of the BGK state only
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -789,11 +965,13 @@ cudaError_t launch_get_tau1(int n, const int* perm, const float4* s, double* ru,
     return cudaGetLastError();
 }
 cudaError_t launch_macroscopics(int model, int n, const int* perm, const float4* f8, const float* f0,
-                                const float4* ruv, float ax, float ay, float* rho, float* ux, float* uy, double* ru,
+                                const float4* ruv, float ax, float ay, const uint16_t* node_sample,
+                                const dev::Collide* coll, float* rho, float* ux, float* uy, double* ru,
                                 cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     if (model == 0)
-        dev::macroscopics_bgk<<<blocks_for(n, 256), 256, 0, st>>>(n, perm, f8, f0, ax, ay, rho, ux, uy, ru);
+        dev::macroscopics_bgk<<<blocks_for(n, 256), 256, 0, st>>>(n, perm, f8, f0, ax, ay, node_sample, coll, rho, ux,
+                                                                   uy, ru);
     else
         dev::macroscopics_tau1<<<blocks_for(n, 256), 256, 0, st>>>(n, perm, ruv, rho, ux, uy, ru);
     return cudaGetLastError();

@@ -20,7 +20,8 @@ cudaError_t launch_set_bgk_equilibrium(int n, const int* perm, const double* ru,
 cudaError_t launch_set_tau1(int n, const int* perm, const double* ru, float4* s, cudaStream_t st);
 cudaError_t launch_get_tau1(int n, const int* perm, const float4* s, double* ru, cudaStream_t st);
 cudaError_t launch_macroscopics(int model, int n, const int* perm, const float4* f8, const float* f0,
-                                const float4* ruv, float ax, float ay, float* rho, float* ux, float* uy, double* ru,
+                                const float4* ruv, float ax, float ay, const uint16_t* node_sample,
+                                const dev::Collide* coll, float* rho, float* ux, float* uy, double* ru,
                                 cudaStream_t st);
 // persistent bulk-copy pipelined step (kernels_tma.cu), variants 4..7
 bool tma_supported(int Kq);

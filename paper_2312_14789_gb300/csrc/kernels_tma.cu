@@ -136,7 +136,7 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty, int s
 template <int KQ, int TN, int STAGES, int MINB>
 __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
     bgk_step_tma(Stencil S, const float4* __restrict__ f8in, const float* __restrict__ f0in,
-                 float4* __restrict__ f8out, float* __restrict__ f0out, Collide C, int n_tiles, int* __restrict__ err) {
+                 float4* __restrict__ f8out, float* __restrict__ f0out, Collide C0, int n_tiles, int* __restrict__ err) {
     using L = Tile<KQ, TN, STAGES>;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBar);
@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
         const int4* sI = reinterpret_cast<const int4*>(st + L::kM);
         const int p = tile * TN + t;
         if (p < S.n) {
+            const Collide C = collide_of(S, C0, p);
             const uint8_t meta = st[L::kM + L::kI + t];
             const int kind = meta & 3;
             float g[9];
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
 // --------------------------------------------------------------- tau = 1
 template <int KQ, int TN, int STAGES, int MINB>
 __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
-    tau1_step_tma(Stencil S, const float4* __restrict__ in, float4* __restrict__ out, Collide C, int n_tiles,
+    tau1_step_tma(Stencil S, const float4* __restrict__ in, float4* __restrict__ out, Collide C0, int n_tiles,
                   int* __restrict__ err) {
     using L = Tile<KQ, TN, STAGES>;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
         const int4* sI = reinterpret_cast<const int4*>(st + L::kM);
         const int p = tile * TN + t;
         if (p < S.n) {
+            const Collide C = collide_of(S, C0, p);
             const uint8_t meta = st[L::kM + L::kI + t];
             const int kind = meta & 3;
             if (kind == 2) {

@@ -38,6 +38,8 @@ struct HostStencils {
     std::vector<double> q;         // [n][9]
     std::vector<double> eqv;       // [n][3] rho_b, ux_b, uy_b
     std::vector<double> area;      // [n]
+    // batches: streaming distance of each node (empty: s for all)
+    std::vector<double> s_node;
     mlbm_stencil_info info{};
 };
 

@@ -198,7 +198,8 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     nodes on a regular row spaced r_coarse*1.19 apart: a parabolic inflow and
     outflow profile with maximum U0 on the left and right, zero velocity on
     the top and bottom, unit density everywhere.  No nodes closer than half
-    the local radius to the cylinder surface.  `scale` < 1 shrinks D and the
+    the local radius to the cylinder surface apart from the wall nodes placed
+    on it (arc spacing about 1.19 r_fine).  `scale` < 1 shrinks D and the
     channel together for small test cases."""
     D = D * scale
     lx, ly = length_d * D, height_d * D
@@ -219,12 +220,19 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     left = np.stack([np.zeros(nby - 1), ys[1:-1]], 1)
     right = np.stack([np.full(nby - 1, lx), ys[1:-1]], 1)
     fixed = np.concatenate([bottom, top, left, right], 0)
-    pts = _sample((0.0, 0.0, lx, ly), (0, 0), rgrid, np.array([[cx, cy, R]]), 0.5, fixed, seed,
-                  max_out=int(4 * lx * ly / r_fine ** 2) + len(fixed) + 1000)
-    n = len(pts)
     nf = len(fixed)
+    # wall nodes on the cylinder surface, arc spacing ~ the fine spacing
+    m = int(round(np.pi * 2 * R / (r_fine * 1.19)))
+    ph = np.random.default_rng(seed).uniform(0, 2 * np.pi)
+    a = ph + 2 * np.pi * np.arange(m) / m
+    surface = np.stack([cx + R * np.cos(a), cy + R * np.sin(a)], 1)
+    pts = _sample((0.0, 0.0, lx, ly), (0, 0), rgrid, np.array([[cx, cy, R]]), 0.5,
+                  np.concatenate([fixed, surface], 0), seed,
+                  max_out=int(4 * lx * ly / r_fine ** 2) + len(fixed) + m + 1000)
+    n = len(pts)
     cls = np.zeros(n, np.uint8)
     cls[:nf] = EQ
+    cls[nf:nf + m] = WALL
     eqv = np.zeros((n, 3))
     eqv[:nf, 0] = 1.0
     side_lr = np.zeros(n, bool)
@@ -240,7 +248,7 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     area *= (lx * ly - np.pi * R * R) / area.sum()
     return Workload(f"karman_D{D:g}_s{seed}", pts, cls, (0.0, 0.0, lx, ly), (OPEN,) * 4,
                     np.array([[cx, cy, R]]), eqv, area, 1.0,
-                    {"D": D, "U0": U0, "H": ly, "L": lx, "seed": seed, "n_eq": nf})
+                    {"D": D, "U0": U0, "H": ly, "L": lx, "seed": seed, "n_eq": nf, "n_wall": m})
 
 
 # --------------------------------------------------------------------------

@@ -87,6 +87,13 @@ def lib():
                 "mlbm_kernel_variant": (_i32, [_vp]),
                 "mlbm_autotune": (st, [_vp, _i32, _vp]),
                 "mlbm_autotune_ex": (st, [_vp, _i32, _i32, _vp]),
+                "mlbm_batch_init": (st, [_vp, _vp, _vp, _i32]),
+                "mlbm_batch_size": (_i32, [_vp]),
+                "mlbm_batch_range": (st, [_vp, _i32, _vp, _vp]),
+                "mlbm_batch_permeability": (st, [_vp, _vp, _vp, _vp, _vp]),
+                "mlbm_batch_run_to_steady": (st, [_vp, _dbl, _i64, _i64, _vp]),
+                "mlbm_batch_drag_lift": (st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+                "mlbm_set_graphs": (st, [_vp, _i32]),
                 "mlbm_reduce_scratch_doubles": (_i64, [_i64]),
                 "mlbm_reduce_fields_device": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
                 "mlbm_reduce_noalloc_max_nodes": (_i64, []),
@@ -299,6 +306,56 @@ def autotune(ctx: Context, steps_per_variant: int = 20, flush_l2: bool = False) 
     ms = ctypes.c_double()
     _check(lib().mlbm_autotune_ex(ctx.handle, int(steps_per_variant), int(bool(flush_l2)), ctypes.byref(ms)))
     return kernel_variant(ctx), ms.value
+
+
+def batch_init(stencils: list, params: list) -> Context:
+    n = len(stencils)
+    arr = (_vp * n)(*[st.handle for st in stencils])
+    P = (_Params * n)(*[_Params(int(p.model), float(p.tau), float(p.tau_minus), float(p.gx), float(p.gy))
+                        for p in params])
+    h = _vp()
+    _check(lib().mlbm_batch_init(ctypes.byref(h), arr, P, n))
+    total = sum(st.n for st in stencils)
+    return Context(h, total, params[0].model, list(stencils))
+
+
+def batch_size(ctx: Context) -> int:
+    return int(lib().mlbm_batch_size(ctx.handle))
+
+
+def batch_range(ctx: Context, sample: int) -> tuple:
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().mlbm_batch_range(ctx.handle, int(sample), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def batch_permeability(ctx: Context) -> dict:
+    m = batch_size(ctx)
+    out = {k: np.empty(m) for k in ("k", "u_superficial", "u_intrinsic", "tortuosity")}
+    _check(lib().mlbm_batch_permeability(ctx.handle, *[_ptr(out[k]) for k in
+                                                       ("k", "u_superficial", "u_intrinsic", "tortuosity")]))
+    return out
+
+
+def batch_run_to_steady(ctx: Context, tol: float, window: int, max_steps: int, raise_on_max: bool = True):
+    taken = np.empty(batch_size(ctx), np.int64)
+    st = lib().mlbm_batch_run_to_steady(ctx.handle, float(tol), int(window), int(max_steps), _ptr(taken))
+    if not (st == 7 and not raise_on_max):
+        _check(st)
+    return taken
+
+
+def batch_drag_lift(ctx: Context, ref_length, u_ref) -> dict:
+    m = batch_size(ctx)
+    L = _f64(np.broadcast_to(np.asarray(ref_length, np.float64), (m,)))
+    U = _f64(np.broadcast_to(np.asarray(u_ref, np.float64), (m,)))
+    out = {k: np.empty(m) for k in ("fx", "fy", "cd", "cl")}
+    _check(lib().mlbm_batch_drag_lift(ctx.handle, _ptr(L), _ptr(U), *[_ptr(out[k]) for k in ("fx", "fy", "cd", "cl")]))
+    return out
+
+
+def set_graphs(ctx: Context, enable: bool):
+    _check(lib().mlbm_set_graphs(ctx.handle, int(bool(enable))))
 
 
 def reduce_scratch_doubles(n: int) -> int:

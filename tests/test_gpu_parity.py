@@ -48,7 +48,7 @@ def gpu_ctx(w, K, s, bb_mode, params, sigma=0.7071067811865476, use_lagrange=Tru
     return ctx
 
 
-VARIANTS = list(range(14))
+VARIANTS = list(range(18))
 
 
 # ----------------------------------------------------------------- plain MLBM
@@ -327,6 +327,31 @@ def test_autotune_keeps_state_and_picks_a_variant():
     mlbm.step(ctx, 5)
     before = mlbm.get_fields(ctx)
     v, ms = mlbm.autotune(ctx, 5)
-    assert 0 <= v <= 13 and ms > 0
+    assert 0 <= v <= 17 and ms > 0
     assert mlbm.step_count(ctx) == 5
     assert np.array_equal(mlbm.get_fields(ctx), before)
+
+
+def test_karman_sweep_batch_full_size_one_step_sampled():
+    """The benchmark's launch configuration: the six (Re, s) vortex-street runs
+    in one batched context at full size, autotuned variant; one step from a
+    random state, 150 sampled nodes of every run (plus link nodes) checked
+    one by one against the oracle."""
+    import bench
+    w = I.karman(seed=2)
+    st_by_s = {s: mlbm.build_stencils_for(w, K=16, s=s, bb_mode=0) for s in sorted({s for _, s in bench.CASES})}
+    sts = [st_by_s[s] for _, s in bench.CASES]
+    params = [mlbm.Params(mlbm.MODEL_BGK, bench.tau_of(re, s), 0.0, 0.0, 0.0) for re, s in bench.CASES]
+    ctx = mlbm.batch_init(sts, params)
+    mlbm.autotune(ctx, 3)
+    f0 = to_f32_state(random_populations(w.n, 41))
+    mlbm.set_populations(ctx, np.tile(f0, (len(bench.CASES), 1)))
+    mlbm.step(ctx, 1)
+    fg = mlbm.get_populations(ctx)
+    for i, (re, s) in enumerate(bench.CASES):
+        first, count = mlbm.batch_range(ctx, i)
+        ex = mlbm.stencils_export(sts[i])
+        t = _sample_targets(w, 150, 50 + i, np.nonzero(ex["link_mask"])[0])
+        op = O.Operator(w, K=16, s=s, bb_mode=0, targets=t).check()
+        fo = O.bgk_step(op, f0, bench.tau_of(re, s))
+        assert np.abs(fg[first:first + count][t] - fo).max() < pop_tol(1), (re, s)
