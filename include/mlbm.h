@@ -213,13 +213,20 @@ mlbm_status mlbm_permeability(mlbm_ctx* ctx, double* k, double* u_superficial, d
 
 /*
  * Step until the relative change of the velocity field over `window` steps,
- * ||u(t) - u(t - window)||_2 / (window ||u(t)||_2), falls below tol (checked
- * every `window` steps), or max_steps is reached (MLBM_E_NOT_CONVERGED).
- * *steps_taken (may be NULL) receives the steps advanced by this call.
- * Returns MLBM_E_DIVERGED on a non-finite velocity norm.
+ * ||u(t) - u(t - window)||_2 / (window ||u(t)||_2) over all nodes but the
+ * equilibrium-overwrite ones, falls below tol, or max_steps is reached
+ * (MLBM_E_NOT_CONVERGED).  t counts from the start of this call; the
+ * criterion is evaluated every `window` steps (mlbm_run_to_steady) or every
+ * `check` steps from t = window on (mlbm_run_to_steady_ex; window must be a
+ * multiple of check; a ring of window / check FP32 velocity snapshots,
+ * 8 bytes per node each, is allocated for the call when check < window and
+ * must stay under 64 GB).  *steps_taken (may be NULL) receives the steps
+ * advanced by this call.  Returns MLBM_E_DIVERGED on a non-finite velocity norm.
  */
 mlbm_status mlbm_run_to_steady(mlbm_ctx* ctx, double tol, int64_t window, int64_t max_steps,
                                int64_t* steps_taken);
+mlbm_status mlbm_run_to_steady_ex(mlbm_ctx* ctx, double tol, int64_t window, int64_t check, int64_t max_steps,
+                                  int64_t* steps_taken);
 
 /* Checkpoint the state, step count and parameters to a file / restore them
    into a context built from the same stencils (node count and K checked). */
@@ -298,6 +305,8 @@ mlbm_status mlbm_batch_drag_lift(mlbm_ctx* ctx, const double* ref_length, const 
    step count at which sample i converged (-1: not converged) */
 mlbm_status mlbm_batch_run_to_steady(mlbm_ctx* ctx, double tol, int64_t window, int64_t max_steps,
                                      int64_t* steps_taken);
+mlbm_status mlbm_batch_run_to_steady_ex(mlbm_ctx* ctx, double tol, int64_t window, int64_t check,
+                                        int64_t max_steps, int64_t* steps_taken);
 
 /* mlbm_step replays chunks of 16 launches from captured CUDA graphs (one per
    starting buffer, re-captured when the variant or stream changes); enable = 0
@@ -342,6 +351,111 @@ mlbm_status mlbm_reduce_fields_device(const float* rho, const float* ux, const f
 int64_t mlbm_reduce_noalloc_max_nodes(void);
 mlbm_status mlbm_reduce_fields_device_noalloc(const float* rho, const float* ux, const float* uy, const float* area,
                                               const uint8_t* mask, int64_t n, double* out, void* stream);
+
+/* ------------------------------------------------------ learned warm start */
+/*
+ * The paper starts every run from rest (Sec. 3.2: body-force driven flow
+ * through porous samples until steady).  The library adds an optional
+ * learned initial state: a per-node multilayer perceptron
+ * 16 -> 64 -> 64 -> 64 -> n_out with ReLU between layers reads 16 local
+ * geometry features (mlbm_features_device) and predicts the steady velocity
+ * (n_out = 2) or the steady velocity and density deviation (n_out = 3) in
+ * units of per-sample scales; the solver then starts from that state instead
+ * of from rest and converges to the same steady state (the prediction only
+ * changes where the iteration starts).  The cold start (rest) stays the
+ * default and the fallback.
+ *
+ * Network: y = x W + b per layer, parameters packed in FP32 in the order
+ * W1[16][64], b1[64], W2[64][64], b2, W3[64][64], b3, W4[64][n_out],
+ * b4[n_out] (mlbm_mlp_param_count(n_out) floats: 9538 for n_out = 2).  The
+ * kernels run the layers on BF16 tensor cores with FP32 accumulation:
+ * features, weights, hidden activations (after bias and ReLU) and, in the
+ * backward pass, the output error and the hidden errors are rounded to BF16
+ * (round to nearest even) where they enter a product; biases, accumulators,
+ * gradients and the Adam state are FP32.  Loss = mean over rows of
+ * |y - t|^2.
+ *
+ * Device arrays: X[n][16], T[n][n_out] and Y[n][n_out], FP32 row-major;
+ * all calls are asynchronous on `stream` (a cudaStream_t, NULL = default
+ * stream) unless they return a host value.  An mlbm_mlp owns its device
+ * memory (created on the current device) and must only be used by one stream
+ * at a time.  Errors: MLBM_E_INVALID (NULL pointers, n or n_out out of
+ * range), MLBM_E_CUDA, MLBM_E_OOM.
+ */
+typedef struct mlbm_mlp mlbm_mlp;
+
+/* parameter count for n_out outputs (1..3), -1 otherwise */
+int64_t mlbm_mlp_param_count(int n_out);
+/* He-normal weights (counter-based generator seeded by `seed`), zero biases;
+   n_out in 1..3. */
+mlbm_status mlbm_mlp_create(mlbm_mlp** out, int n_out, uint64_t seed);
+void mlbm_mlp_destroy(mlbm_mlp* m);
+/* n_out of the network (-1 for NULL) */
+int mlbm_mlp_outputs(const mlbm_mlp* m);
+/* host FP32 params[mlbm_mlp_param_count(n_out)]; set also resets the Adam state */
+mlbm_status mlbm_mlp_set_params(mlbm_mlp* m, const float* params);
+mlbm_status mlbm_mlp_get_params(mlbm_mlp* m, float* params);
+/* Y[n][n_out] = network(X[n][16]); n >= 0. */
+mlbm_status mlbm_mlp_forward_device(mlbm_mlp* m, const float* X, int64_t n, float* Y, void* stream);
+/* Full-batch gradient of the loss over all n rows into grads (device,
+   param_count floats, packed order; NULL: kept internally) and the loss
+   (host double, NULL: not returned; returning it synchronises `stream`).
+   Reproducible: per-block partial sums are added in a fixed order. */
+mlbm_status mlbm_mlp_gradients_device(mlbm_mlp* m, const float* X, const float* T, int64_t n, float* grads,
+                                      double* loss, void* stream);
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected,
+   learning rate lr) on minibatches of `batch` rows drawn with replacement
+   from the n rows by a counter-based hash of (seed, step, row); batch = n
+   with seed = 0 takes every row once per step (full batch).  loss (host,
+   nullable) receives the mean loss of the last minibatch, evaluated with
+   the parameters before its update. */
+mlbm_status mlbm_mlp_train_device(mlbm_mlp* m, const float* X, const float* T, int64_t n, int64_t batch,
+                                  int64_t steps, float lr, uint64_t seed, double* loss, void* stream);
+
+/*
+ * Geometry features of every node, X[n][16] (device, FP32, caller's node
+ * order), for the node set and geometry of mlbm_build_stencils, with length
+ * scale L > 0 (the library's studies use the mean disk radius) and
+ * ell = min(8 L, half the smaller box extent):
+ *   0   clamp(d1 / L, 0, 4)   d1 = distance to the nearest solid surface
+ *                             (disk, or periodic image of a disk, or solid side)
+ *   1,2 unit vector from that surface point to the node (0 if no solid)
+ *   3   clamp(d2 / L, 0, 4)   d2 = distance to the second nearest solid object
+ *   4..7 free paths along +x, -x, +y, -y (distance to the first solid along
+ *        the ray, at most ell) over L; a ray starting on a surface and
+ *        pointing out of the solid does not meet it
+ *   8   clamp(f(+y) f(-y) / L^2, 0, 16), 9  clamp((f(+y) + f(-y)) / L, 0, 8)
+ *   10..13 local porosity 1 - (solid area within distance rho_j of the node)
+ *         / (pi rho_j^2), rho_j = min(c_j L, half the smaller box extent),
+ *         c_j = 1, 2, 4, 8: disks (with their periodic images) cut by the
+ *         circle in closed form (circle-circle lens), solid sides as
+ *         circular segments;
+ *   14  porosity of the box, 1 - sum(pi r^2) / box area
+ *   15  4 (y - y0) (y1 - y) / (y1 - y0)^2 (position across the box)
+ * With no solid object d1 = d2 = 4 L.  Computed in FP64 on the device.
+ * Inputs are host arrays (copied to the device inside); synchronous.
+ * Errors: MLBM_E_INVALID, MLBM_E_CUDA.
+ */
+mlbm_status mlbm_features_device(const mlbm_nodes* nodes, const mlbm_geometry* geo, double L, float* X);
+
+/*
+ * Warm start: sets the state of ctx from the network's prediction Y =
+ * network(X) for every node but the equilibrium-overwrite ones (those take
+ * their boundary values): u = scale_u[s] * (Y0, Y1) and, when the network
+ * has 3 outputs, rho = 1 + scale_rho[s] * Y2 minus the area-weighted mean of
+ * that deviation over the sample (the sample keeps the mass of the rest
+ * state); with 2 outputs rho = 1.  BGK contexts start from the equilibrium
+ * of that state, as mlbm_set_fields.  X[n][16] (device, caller's node order;
+ * for a batch the samples' rows one after another); scale_u[] and
+ * scale_rho[] host, one per sample (scale_rho may be NULL with 2 outputs).
+ * A sample whose prediction holds a non-finite value, a speed above 0.3
+ * (outside the low-Mach range of the scheme) or a density deviation above
+ * 0.1 starts from rest instead (the cold-start fallback); n_cold (nullable)
+ * receives the number of such samples.  Resets the step count; synchronous.
+ * Errors: MLBM_E_INVALID, MLBM_E_CUDA.
+ */
+mlbm_status mlbm_warm_start(mlbm_ctx* ctx, mlbm_mlp* m, const float* X, const double* scale_u,
+                            const double* scale_rho, int* n_cold);
 
 /* Last error message of this thread ("" when none). */
 const char* mlbm_last_error(void);

@@ -1,7 +1,7 @@
 """FP64 CPU oracle of the warm-start MLP -- TEST INFRASTRUCTURE ONLY.
 
-A per-node multilayer perceptron 16 -> 64 -> 64 -> 64 -> 2 with ReLU between
-layers (y = x W + b per layer, W stored [in][out]), mean-squared-error loss
+A per-node multilayer perceptron 16 -> 64 -> 64 -> 64 -> n_out (n_out = 2:
+velocity; 3: velocity and density) with ReLU between layers (y = x W + b per layer, W stored [in][out]), mean-squared-error loss
 and Adam.  Plain numpy in float64.  `bf16=True` rounds to bfloat16
 (round-to-nearest-even) at the points where a BF16 tensor-core
 implementation rounds its operands: the layer inputs (features and every
@@ -19,6 +19,10 @@ import numpy as np
 SIZES = (16, 64, 64, 64, 2)
 
 
+def sizes(n_out=2):
+    return SIZES[:-1] + (int(n_out),)
+
+
 def bf16(x):
     """Round float64 values to the nearest bfloat16 (ties to even) via float32."""
     f = np.asarray(x, dtype=np.float32)
@@ -28,11 +32,12 @@ def bf16(x):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def init_params(seed: int):
+def init_params(seed: int, n_out: int = 2):
     """He-normal weights, zero biases, from a seeded generator."""
     rng = np.random.default_rng(seed)
     params = []
-    for a, b in zip(SIZES[:-1], SIZES[1:]):
+    S = sizes(n_out)
+    for a, b in zip(S[:-1], S[1:]):
         params.append(rng.normal(0.0, np.sqrt(2.0 / a), size=(a, b)))
         params.append(np.zeros(b))
     return params
@@ -42,16 +47,18 @@ def pack(params):
     return np.concatenate([p.ravel() for p in params])
 
 
-def unpack(vec):
+def unpack(vec, n_out: int = 2):
     out, o = [], 0
-    for a, b in zip(SIZES[:-1], SIZES[1:]):
+    S = sizes(n_out)
+    for a, b in zip(S[:-1], S[1:]):
         out.append(np.asarray(vec[o:o + a * b], dtype=np.float64).reshape(a, b)); o += a * b
         out.append(np.asarray(vec[o:o + b], dtype=np.float64)); o += b
     return out
 
 
-def n_params():
-    return sum(a * b + b for a, b in zip(SIZES[:-1], SIZES[1:]))
+def n_params(n_out: int = 2):
+    S = sizes(n_out)
+    return sum(a * b + b for a, b in zip(S[:-1], S[1:]))
 
 
 def forward(params, X, bf16_round=False):

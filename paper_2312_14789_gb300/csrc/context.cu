@@ -57,6 +57,7 @@ struct mlbm_ctx {
     int64_t scratch_len = 0;
     double* small = nullptr;
     int64_t steps = 0;
+    int64_t steps_in_last_run = 0;  // steps taken by the last run to steady state
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = -1.0;
@@ -352,6 +353,77 @@ mlbm_status fields_to_work(mlbm_ctx* c, double* ru_dev_or_null) {
     return MLBM_OK;
 }
 
+// Steady-state iteration shared by the single and batched entry points: every
+// `check` steps each sample's velocity is compared with its own snapshot of
+// `window` steps earlier (a ring of window / check snapshots), delta =
+// |u(t) - u(t - window)|_2 / (window |u(t)|_2) over non-equilibrium nodes;
+// a sample is steady at the first t >= window with delta < tol.  at[i]
+// receives that t, or -1.  Steps stop once every sample is steady.
+mlbm_status run_steady(mlbm_ctx* c, double tol, int64_t window, int64_t check, int64_t max_steps, int64_t* at,
+                       const char* name) {
+    const std::string nm(name);
+    if (!(tol > 0) || window < 1 || check < 1 || window % check != 0 || max_steps < 0)
+        return set_error(MLBM_E_INVALID, nm + ": bad arguments (window must be a positive multiple of check)");
+    const int ns = (int)c->seg_off.size() - 1;
+    const int64_t R = window / check;
+    const int64_t n = c->n;
+    std::vector<int64_t> done_at(ns, -1);
+    c->steps_in_last_run = 0;
+    float* ring = nullptr;
+    if (R > 1) {
+        if ((double)R * 2.0 * (double)n * 4.0 > 64e9)
+            return set_error(MLBM_E_INVALID, nm + ": snapshot ring over 64 GB (use a larger check interval)");
+        MLBM_CUDA(cudaMallocAsync(&ring, (size_t)R * 2 * (size_t)n * sizeof(float), c->stream));
+    }
+    auto slot_u = [&](int64_t k) { return R > 1 ? ring + (size_t)k * 2 * n : c->px; };
+    auto slot_v = [&](int64_t k) { return R > 1 ? ring + ((size_t)k * 2 + 1) * n : c->py; };
+    std::vector<double> h(2 * (size_t)ns);
+    auto snapshot = [&](int64_t k, bool read) -> mlbm_status {
+        MLBM_TRY(fields_to_work(c, nullptr));
+        for (int i = 0; i < ns; ++i) {
+            const int64_t o = c->seg_off[i], m = c->seg_off[i + 1] - o;
+            MLBM_CUDA(launch_change(c->ux + o, c->uy + o, slot_u(k) + o, slot_v(k) + o, c->mask + o, m, c->scratch,
+                                    c->seg_out + 2 * i, c->stream));
+        }
+        if (read) MLBM_CUDA(cudaMemcpyAsync(h.data(), c->seg_out, 16 * (size_t)ns, cudaMemcpyDeviceToHost, c->stream));
+        return sync(c);
+    };
+    auto body = [&]() -> mlbm_status {
+        MLBM_TRY(snapshot(0, false));
+        int64_t t = 0;
+        int remaining = ns;
+        while (t < max_steps && remaining > 0) {
+            const int64_t w = std::min(check, max_steps - t);
+            MLBM_TRY(mlbm_step(c, w));
+            t += w;
+            c->steps_in_last_run = t;
+            if (w != check) break;  // a partial chunk at max_steps is not evaluated
+            const bool eval = t >= window;
+            MLBM_TRY(snapshot((t / check) % R, eval));
+            if (!eval) continue;
+            for (int i = 0; i < ns; ++i) {
+                if (done_at[i] >= 0) continue;
+                if (!std::isfinite(h[2 * i]) || !std::isfinite(h[2 * i + 1]))
+                    return set_error(MLBM_E_DIVERGED, nm + ": non-finite velocity in sample " + std::to_string(i));
+                const double delta = h[2 * i + 1] > 0 ? std::sqrt(h[2 * i] / h[2 * i + 1]) / (double)window : 0.0;
+                if (delta < tol) {
+                    done_at[i] = t;
+                    --remaining;
+                }
+            }
+        }
+        return remaining == 0 ? MLBM_OK : set_error(MLBM_E_NOT_CONVERGED, nm + ": max_steps reached");
+    };
+    mlbm_status st = body();
+    if (ring) {
+        cudaFreeAsync(ring, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    if (at)
+        for (int i = 0; i < ns; ++i) at[i] = done_at[i];
+    return st;
+}
+
 }  // namespace
 
 
@@ -542,29 +614,17 @@ mlbm_status mlbm_permeability(mlbm_ctx* c, double* k, double* us, double* ui, do
 }
 
 mlbm_status mlbm_run_to_steady(mlbm_ctx* c, double tol, int64_t window, int64_t max_steps, int64_t* taken) {
+    return mlbm_run_to_steady_ex(c, tol, window, window, max_steps, taken);
+}
+
+mlbm_status mlbm_run_to_steady_ex(mlbm_ctx* c, double tol, int64_t window, int64_t check, int64_t max_steps,
+                                  int64_t* taken) {
     if (!c) return set_error(MLBM_E_INVALID, "run_to_steady: NULL context");
-    if (!(tol > 0) || window < 1 || max_steps < 0) return set_error(MLBM_E_INVALID, "run_to_steady: bad arguments");
-    int64_t done = 0;
     if (taken) *taken = 0;
-    // reference snapshot u(t0)
-    MLBM_TRY(fields_to_work(c, nullptr));
-    MLBM_CUDA(launch_change(c->ux, c->uy, c->px, c->py, c->mask, c->n, c->scratch, c->small, c->stream));
-    while (done < max_steps) {
-        const int64_t w = std::min(window, max_steps - done);
-        MLBM_TRY(mlbm_step(c, w));
-        done += w;
-        if (taken) *taken = done;
-        MLBM_TRY(fields_to_work(c, nullptr));
-        MLBM_CUDA(launch_change(c->ux, c->uy, c->px, c->py, c->mask, c->n, c->scratch, c->small, c->stream));
-        double h[2];
-        MLBM_CUDA(cudaMemcpyAsync(h, c->small, 16, cudaMemcpyDeviceToHost, c->stream));
-        MLBM_TRY(sync(c));
-        if (!std::isfinite(h[0]) || !std::isfinite(h[1]))
-            return set_error(MLBM_E_DIVERGED, "run_to_steady: non-finite velocity field");
-        const double delta = h[1] > 0 ? std::sqrt(h[0] / h[1]) / (double)w : 0.0;
-        if (w == window && delta < tol) return MLBM_OK;
-    }
-    return set_error(MLBM_E_NOT_CONVERGED, "run_to_steady: max_steps reached");
+    int64_t at = -1;
+    mlbm_status st = run_steady(c, tol, window, check, max_steps, &at, "run_to_steady");
+    if (taken) *taken = at >= 0 ? at : c->steps_in_last_run;
+    return st;
 }
 
 mlbm_status mlbm_save(mlbm_ctx* c, const char* path) {
@@ -884,43 +944,13 @@ mlbm_status mlbm_batch_permeability(mlbm_ctx* c, double* k, double* us, double* 
 }
 
 mlbm_status mlbm_batch_run_to_steady(mlbm_ctx* c, double tol, int64_t window, int64_t max_steps, int64_t* taken) {
+    return mlbm_batch_run_to_steady_ex(c, tol, window, window, max_steps, taken);
+}
+
+mlbm_status mlbm_batch_run_to_steady_ex(mlbm_ctx* c, double tol, int64_t window, int64_t check, int64_t max_steps,
+                                        int64_t* taken) {
     if (!c) return set_error(MLBM_E_INVALID, "batch_run_to_steady: NULL context");
-    if (!(tol > 0) || window < 1 || max_steps < 0) return set_error(MLBM_E_INVALID, "batch_run_to_steady: bad arguments");
-    const int ns = (int)c->seg_off.size() - 1;
-    std::vector<int64_t> at(ns, -1);
-    auto snapshot = [&](double* host) -> mlbm_status {
-        MLBM_TRY(fields_to_work(c, nullptr));
-        for (int i = 0; i < ns; ++i) {
-            const int64_t o = c->seg_off[i], m = c->seg_off[i + 1] - o;
-            MLBM_CUDA(launch_change(c->ux + o, c->uy + o, c->px + o, c->py + o, c->mask + o, m, c->scratch,
-                                    c->seg_out + 2 * i, c->stream));
-        }
-        if (host) MLBM_CUDA(cudaMemcpyAsync(host, c->seg_out, 16 * (size_t)ns, cudaMemcpyDeviceToHost, c->stream));
-        return sync(c);
-    };
-    MLBM_TRY(snapshot(nullptr));
-    int64_t done = 0;
-    int remaining = ns;
-    std::vector<double> h(2 * (size_t)ns);
-    while (done < max_steps && remaining > 0) {
-        const int64_t w = std::min(window, max_steps - done);
-        MLBM_TRY(mlbm_step(c, w));
-        done += w;
-        MLBM_TRY(snapshot(h.data()));
-        for (int i = 0; i < ns; ++i) {
-            if (at[i] >= 0) continue;
-            if (!std::isfinite(h[2 * i]) || !std::isfinite(h[2 * i + 1]))
-                return set_error(MLBM_E_DIVERGED, "batch_run_to_steady: non-finite velocity in sample " + std::to_string(i));
-            const double delta = h[2 * i + 1] > 0 ? std::sqrt(h[2 * i] / h[2 * i + 1]) / (double)w : 0.0;
-            if (w == window && delta < tol) {
-                at[i] = done;
-                --remaining;
-            }
-        }
-    }
-    if (taken)
-        for (int i = 0; i < ns; ++i) taken[i] = at[i];
-    return remaining == 0 ? MLBM_OK : set_error(MLBM_E_NOT_CONVERGED, "batch_run_to_steady: max_steps reached");
+    return run_steady(c, tol, window, check, max_steps, taken, "batch_run_to_steady");
 }
 
 mlbm_status mlbm_batch_drag_lift(mlbm_ctx* c, const double* ref_length, const double* u_ref, double* fx, double* fy,
@@ -960,6 +990,82 @@ mlbm_status mlbm_batch_drag_lift(mlbm_ctx* c, const double* ref_length, const do
         if (cd) cd[i] = den != 0 ? 2.0 * Fx / den : 0.0;
         if (cl) cl[i] = den != 0 ? 2.0 * Fy / den : 0.0;
     }
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_warm_start(mlbm_ctx* c, mlbm_mlp* m, const float* X, const double* scale_u,
+                            const double* scale_rho, int* n_cold) {
+    if (!c || !m || !X || !scale_u) return set_error(MLBM_E_INVALID, "warm_start: NULL argument");
+    const int no = mlbm_mlp_outputs(m);
+    if (no != 2 && no != 3) return set_error(MLBM_E_INVALID, "warm_start: the network must have 2 or 3 outputs");
+    if (no == 3 && !scale_rho) return set_error(MLBM_E_INVALID, "warm_start: NULL density scale");
+    const int ns = (int)c->seg_off.size() - 1;
+    for (int i = 0; i < ns; ++i)
+        if (!std::isfinite(scale_u[i]) || (no == 3 && !std::isfinite(scale_rho[i])))
+            return set_error(MLBM_E_INVALID, "warm_start: non-finite scale");
+    if (n_cold) *n_cold = 0;
+    const int n = (int)c->n;
+    // one temporary buffer: scales (2 ns doubles), density means (ns
+    // doubles), flags (ns ints), then the prediction Y[n][no] (16-byte aligned)
+    const size_t head = ((size_t)ns * 28 + 15) / 16 * 16;
+    void* buf = nullptr;
+    MLBM_CUDA(cudaMallocAsync(&buf, head + (size_t)n * no * sizeof(float) + 16, c->stream));
+    double* dscale_u = static_cast<double*>(buf);
+    double* dscale_r = dscale_u + ns;
+    double* dmean = dscale_r + ns;
+    int* flag = reinterpret_cast<int*>(dmean + ns);
+    float* Y = reinterpret_cast<float*>(static_cast<char*>(buf) + head);
+    // releases the temporary buffer (stream-ordered) and passes a status on
+    auto release = [&](mlbm_status s) {
+        cudaFreeAsync(buf, c->stream);
+        return s;
+    };
+    std::vector<double> hs(2 * (size_t)ns, 0.0);
+    for (int i = 0; i < ns; ++i) {
+        hs[i] = scale_u[i];
+        hs[ns + i] = no == 3 ? scale_rho[i] : 0.0;
+    }
+    cudaError_t e = cudaMemcpyAsync(dscale_u, hs.data(), 16 * (size_t)ns, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, (size_t)ns * 4, c->stream);
+    if (e != cudaSuccess) return release(set_error(MLBM_E_CUDA, std::string("warm_start: ") + cudaGetErrorString(e)));
+    mlbm_status st = mlbm_mlp_forward_device(m, X, n, Y, c->stream);
+    if (st != MLBM_OK) return release(st);
+    e = launch_warm_check(n, c->perm, c->S.node_sample, c->meta, Y, no, dscale_u, dscale_r, 0.3f, 0.1f, flag,
+                          c->stream);
+    std::vector<double> hmean(ns, 0.0);
+    if (e == cudaSuccess && no == 3) {
+        // area-weighted mean of the predicted density deviation per sample
+        e = launch_warm_drho(n, c->perm, c->S.node_sample, c->meta, Y, no, dscale_r, c->rho, c->stream);
+        std::vector<double> sums(6 * (size_t)ns);
+        for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+            const int64_t o = c->seg_off[i], cnt = c->seg_off[i + 1] - o;
+            e = launch_reduce_fields(c->rho + o, c->ux + o, c->uy + o, c->area + o, c->mask + o, cnt, c->scratch,
+                                     c->seg_out + 6 * i, c->stream);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sums.data(), c->seg_out, 48 * (size_t)ns, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        for (int i = 0; i < ns && e == cudaSuccess; ++i) hmean[i] = sums[6 * i] > 0 ? sums[6 * i + 1] / sums[6 * i] : 0.0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dmean, hmean.data(), 8 * (size_t)ns, cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e == cudaSuccess)
+        e = launch_warm_fill(n, c->perm, c->S.node_sample, c->meta, c->eqv, Y, no, dscale_u, c->rho, dmean, flag, c->io,
+                             c->stream);
+    if (e == cudaSuccess) {
+        if (c->params.model == MLBM_MODEL_BGK)
+            e = launch_set_bgk_equilibrium(n, c->perm, c->io, c->f8[c->cur], c->f0[c->cur], c->stream);
+        else
+            e = launch_set_tau1(n, c->perm, c->io, c->ruv[c->cur], c->stream);
+    }
+    std::vector<int> hflag(ns, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflag.data(), flag, (size_t)ns * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return release(set_error(MLBM_E_CUDA, std::string("warm_start: ") + cudaGetErrorString(e)));
+    MLBM_TRY(release(MLBM_OK));
+    MLBM_TRY(sync(c));
+    if (n_cold)
+        for (int i = 0; i < ns; ++i) *n_cold += hflag[i] != 0;
+    c->steps = 0;
     return MLBM_OK;
 }
 

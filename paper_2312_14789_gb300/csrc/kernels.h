@@ -40,4 +40,14 @@ cudaError_t launch_reduce_fields(const float* rho, const float* ux, const float*
 cudaError_t launch_change(const float* ux, const float* uy, float* px, float* py, const uint8_t* mask, int64_t n,
                           double* partial, double* out, cudaStream_t st);
 
+// warm start (features.cu)
+cudaError_t launch_warm_check(int n, const int* perm, const uint16_t* node_sample, const uint8_t* meta,
+                              const float* Y, int no, const double* scale_u, const double* scale_rho, float umax,
+                              float drho_max, int* flag, cudaStream_t st);
+cudaError_t launch_warm_drho(int n, const int* perm, const uint16_t* node_sample, const uint8_t* meta,
+                             const float* Y, int no, const double* scale_rho, float* drho, cudaStream_t st);
+cudaError_t launch_warm_fill(int n, const int* perm, const uint16_t* node_sample, const uint8_t* meta,
+                             const float4* eqv, const float* Y, int no, const double* scale_u, const float* drho,
+                             const double* drho_mean, const int* flag, double* ru, cudaStream_t st);
+
 }  // namespace mlbm

@@ -79,6 +79,7 @@ def lib():
                 "mlbm_drag_lift": (st, [_vp, _dbl, _dbl, _vp, _vp, _vp, _vp]),
                 "mlbm_permeability": (st, [_vp, _vp, _vp, _vp, _vp]),
                 "mlbm_run_to_steady": (st, [_vp, _dbl, _i64, _i64, _vp]),
+                "mlbm_run_to_steady_ex": (st, [_vp, _dbl, _i64, _i64, _i64, _vp]),
                 "mlbm_save": (st, [_vp, ctypes.c_char_p]),
                 "mlbm_load": (st, [_vp, ctypes.c_char_p]),
                 "mlbm_set_timing": (st, [_vp, _i32]),
@@ -92,12 +93,25 @@ def lib():
                 "mlbm_batch_range": (st, [_vp, _i32, _vp, _vp]),
                 "mlbm_batch_permeability": (st, [_vp, _vp, _vp, _vp, _vp]),
                 "mlbm_batch_run_to_steady": (st, [_vp, _dbl, _i64, _i64, _vp]),
+                "mlbm_batch_run_to_steady_ex": (st, [_vp, _dbl, _i64, _i64, _i64, _vp]),
                 "mlbm_batch_drag_lift": (st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
                 "mlbm_set_graphs": (st, [_vp, _i32]),
                 "mlbm_reduce_scratch_doubles": (_i64, [_i64]),
                 "mlbm_reduce_fields_device": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
                 "mlbm_reduce_noalloc_max_nodes": (_i64, []),
                 "mlbm_reduce_fields_device_noalloc": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+                "mlbm_mlp_param_count": (_i64, [_i32]),
+                "mlbm_mlp_create": (st, [_vp, _i32, ctypes.c_uint64]),
+                "mlbm_mlp_destroy": (None, [_vp]),
+                "mlbm_mlp_outputs": (_i32, [_vp]),
+                "mlbm_mlp_set_params": (st, [_vp, _vp]),
+                "mlbm_mlp_get_params": (st, [_vp, _vp]),
+                "mlbm_mlp_forward_device": (st, [_vp, _vp, _i64, _vp, _vp]),
+                "mlbm_mlp_gradients_device": (st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+                "mlbm_mlp_train_device": (st, [_vp, _vp, _vp, _i64, _i64, _i64, ctypes.c_float, ctypes.c_uint64,
+                                               _vp, _vp]),
+                "mlbm_features_device": (st, [_vp, _vp, _dbl, _vp]),
+                "mlbm_warm_start": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
                 "mlbm_last_error": (ctypes.c_char_p, []),
                 "mlbm_version": (ctypes.c_char_p, []),
             }
@@ -268,9 +282,12 @@ def permeability(ctx: Context):
     return {"k": k, "u_superficial": us, "u_intrinsic": ui, "tortuosity": tv}
 
 
-def run_to_steady(ctx: Context, tol: float, window: int, max_steps: int, raise_on_max: bool = True) -> int:
+def run_to_steady(ctx: Context, tol: float, window: int, max_steps: int, raise_on_max: bool = True,
+                  check: int | None = None) -> int:
+    """Steps to steady state (criterion checked every `check` steps, default `window`)."""
     taken = ctypes.c_int64()
-    st = lib().mlbm_run_to_steady(ctx.handle, float(tol), int(window), int(max_steps), ctypes.byref(taken))
+    st = lib().mlbm_run_to_steady_ex(ctx.handle, float(tol), int(window), int(check or window), int(max_steps),
+                                     ctypes.byref(taken))
     if st == 7 and not raise_on_max:
         return -int(taken.value)
     _check(st)
@@ -337,9 +354,11 @@ def batch_permeability(ctx: Context) -> dict:
     return out
 
 
-def batch_run_to_steady(ctx: Context, tol: float, window: int, max_steps: int, raise_on_max: bool = True):
+def batch_run_to_steady(ctx: Context, tol: float, window: int, max_steps: int, raise_on_max: bool = True,
+                        check: int | None = None):
     taken = np.empty(batch_size(ctx), np.int64)
-    st = lib().mlbm_batch_run_to_steady(ctx.handle, float(tol), int(window), int(max_steps), _ptr(taken))
+    st = lib().mlbm_batch_run_to_steady_ex(ctx.handle, float(tol), int(window), int(check or window),
+                                           int(max_steps), _ptr(taken))
     if not (st == 7 and not raise_on_max):
         _check(st)
     return taken
@@ -376,3 +395,82 @@ def reduce_fields_device_noalloc(rho_ptr, ux_ptr, uy_ptr, area_ptr, mask_ptr, n,
     _check(lib().mlbm_reduce_fields_device_noalloc(_vp(rho_ptr), _vp(ux_ptr), _vp(uy_ptr), _vp(area_ptr),
                                                    _vp(mask_ptr) if mask_ptr else None, int(n), _vp(out_ptr),
                                                    _vp(stream_handle) if stream_handle else None))
+
+
+# ------------------------------------------------------- learned warm start
+# Device arrays are passed as integer device addresses (e.g. a torch CUDA
+# tensor's .data_ptr()); streams as cudaStream_t handles (None: default).
+def _sp(stream_handle):
+    return _vp(stream_handle) if stream_handle else None
+
+
+class Mlp:
+    """Handle of the library's warm-start network (16-64-64-64-n_out)."""
+
+    def __init__(self, seed: int = 1, n_out: int = 2):
+        h = _vp()
+        _check(lib().mlbm_mlp_create(ctypes.byref(h), int(n_out), ctypes.c_uint64(int(seed))))
+        self.handle = h
+        self.n_out = int(n_out)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.mlbm_mlp_destroy(self.handle)
+            self.handle = None
+
+    def param_count(self) -> int:
+        return int(lib().mlbm_mlp_param_count(self.n_out))
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        if a.size != self.param_count():
+            raise ValueError(f"expected {self.param_count()} parameters, got {a.size}")
+        _check(lib().mlbm_mlp_set_params(self.handle, _ptr(a)))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.param_count(), np.float32)
+        _check(lib().mlbm_mlp_get_params(self.handle, _ptr(a)))
+        return a
+
+    def forward(self, X_ptr, n, Y_ptr, stream_handle=None):
+        _check(lib().mlbm_mlp_forward_device(self.handle, _vp(X_ptr), int(n), _vp(Y_ptr), _sp(stream_handle)))
+
+    def gradients(self, X_ptr, T_ptr, n, grads_ptr=None, stream_handle=None) -> float:
+        loss = ctypes.c_double()
+        _check(lib().mlbm_mlp_gradients_device(self.handle, _vp(X_ptr), _vp(T_ptr), int(n),
+                                               _vp(grads_ptr) if grads_ptr else None, ctypes.byref(loss),
+                                               _sp(stream_handle)))
+        return loss.value
+
+    def train(self, X_ptr, T_ptr, n, batch, steps, lr, seed, stream_handle=None) -> float:
+        loss = ctypes.c_double()
+        _check(lib().mlbm_mlp_train_device(self.handle, _vp(X_ptr), _vp(T_ptr), int(n), int(batch), int(steps),
+                                           ctypes.c_float(lr), ctypes.c_uint64(int(seed)),
+                                           ctypes.byref(loss) if steps > 0 else None, _sp(stream_handle)))
+        return loss.value
+
+
+def features_device(xy, box, sides, disks, L, X_ptr):
+    """Geometry features [n][16] (FP32) of nodes xy into device memory X_ptr."""
+    xy = _f64(xy)
+    dk = _f64(np.zeros((0, 3)) if disks is None else np.asarray(disks).reshape(-1, 3))
+    nodes = _Nodes(xy.shape[0], _ptr(xy), None, None, None)
+    geo = _Geometry(float(box[0]), float(box[1]), float(box[2]), float(box[3]), (_i32 * 4)(*[int(v) for v in sides]),
+                    len(dk), _ptr(dk) if len(dk) else None)
+    _check(lib().mlbm_features_device(ctypes.byref(nodes), ctypes.byref(geo), float(L), _vp(X_ptr)))
+
+
+def features_for(w, L, X_ptr):
+    """features_device for an inputs.Workload."""
+    features_device(w.xy, w.box, w.sides, w.disks, L, X_ptr)
+
+
+def warm_start(ctx: Context, mlp: Mlp, X_ptr, scale_u, scale_rho=None) -> int:
+    """Start ctx from the network's prediction (u = scale_u * Y[:, :2] and,
+    with 3 outputs, rho = 1 + scale_rho * Y[:, 2] minus its sample mean);
+    returns how many samples fell back to rest."""
+    su = _f64(np.atleast_1d(np.asarray(scale_u, np.float64)))
+    sr = None if scale_rho is None else _f64(np.atleast_1d(np.asarray(scale_rho, np.float64)))
+    cold = ctypes.c_int()
+    _check(lib().mlbm_warm_start(ctx.handle, mlp.handle, _vp(X_ptr), _ptr(su), _ptr(sr), ctypes.byref(cold)))
+    return cold.value

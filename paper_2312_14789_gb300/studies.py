@@ -1,6 +1,7 @@
 """Measurement studies beyond the single-workload benchmark.
 
     python -m paper_2312_14789_gb300.studies batch [--samples 64] [--steps 20]
+    python -m paper_2312_14789_gb300.studies warm [--train 512] [--test 64] [--nodes 200000]
 
 batch: 64 porous samples (seeds 1000..1063) with node counts U(50k, 400k),
 porosity U(0.5, 0.85) and a mix of Darcy (s = 1) and inertial (s = 1/2, 1/4)
@@ -9,7 +10,18 @@ Reports the aggregate node-updates/s of the batched context (all samples in
 the same launches, CUDA-graph replay) against the sum of sequential
 single-instance runs of the same samples, each timed with CUDA events.
 
-Prints one JSON line.
+warm: learned warm start.  Porous samples (porosity 0.7, radii U(8, 16),
+seeds 10000.. for training and 20000.. held out), MLBM1 (tau = 1), s = 1,
+K = 16, interpolated bounce-back, body force g = 1e-6 along x (Darcy).
+Training samples are solved from rest to steady state (|u(t) - u(t-1000)| /
+(1000 |u(t)|) < 1e-7) in batches, stencil builds of the next batch
+overlapping the solves; the network is trained on their features and
+normalised steady velocities; the held-out samples are then solved from rest,
+from the network's prediction and from a uniform Kozeny-Carman estimate.
+Reports steps and seconds to steady state, permeability differences against
+the cold start and the prediction error.
+
+Each study prints one JSON line.
 """
 from __future__ import annotations
 
@@ -104,15 +116,165 @@ def batch_study(args):
     print(json.dumps(out))
 
 
+def warm_study(args):
+    import concurrent.futures as cf
+
+    import torch
+    from paper_2312_14789_gb300 import mlbm
+    from paper_2312_14789_gb300 import warmstart as W
+
+    log = (lambda m: print(m, file=sys.stderr, flush=True))
+    t_all = time.time()
+    train_seeds = list(range(10000, 10000 + args.train))
+    test_seeds = list(range(20000, 20000 + args.test))
+    t0 = time.time()
+    ws_train = W.make_samples(train_seeds, args.nodes)
+    ws_test = W.make_samples(test_seeds, args.nodes)
+    t_gen = time.time() - t0
+    log(f"generated {len(ws_train)} + {len(ws_test)} samples in {t_gen:.1f} s")
+    par = lambda ws: [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, args.g, 0.0) for _ in ws]
+
+    # ---- training data: batched cold solves, next group's stencils built meanwhile
+    groups = [ws_train[i:i + args.group] for i in range(0, len(ws_train), args.group)]
+    X_parts, T_parts, train_steps = [], [], []
+    t_solve = t_build = 0.0
+    with cf.ThreadPoolExecutor(1) as ex:
+        def timed_build(ws):
+            t = time.time()
+            return W.build(ws), time.time() - t
+        fut = ex.submit(timed_build, groups[0])
+        for gi, ws in enumerate(groups):
+            sts, tb = fut.result()
+            t_build += tb
+            if gi + 1 < len(groups):
+                fut = ex.submit(timed_build, groups[gi + 1])
+            ps = par(ws)
+            ru, steps, sec, _ = W.solve(sts, ps)
+            t_solve += sec
+            train_steps += list(steps)
+            X_parts.append(W.features(ws))
+            T_parts.append(torch.from_numpy(W.targets(ws, ru, ps, 3)).cuda())
+            del sts
+            log(f"group {gi}: {sum(w.n for w in ws)} nodes, steps {int(np.mean(steps))} mean, {sec:.1f} s")
+    X = torch.cat(X_parts)
+    T = torch.cat(T_parts)
+    del X_parts, T_parts
+    n_rows = X.shape[0]
+
+    # ---- training: a velocity-only network (2 outputs) and a velocity +
+    # density network (3 outputs) on the same rows
+    T2 = T[:, :2].contiguous()
+    t_var = {"velocity": float(((T2 - T2.mean(0)) ** 2).sum(1).mean()),
+             "density": float(((T[:, 2] - T[:, 2].mean()) ** 2).mean())}
+    nets, train_info = {}, {}
+    for no, TT in ((2, T2), (3, T)):
+        net = mlbm.Mlp(args.seed, no)
+        l0 = net.gradients(X.data_ptr(), TT.data_ptr(), n_rows)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        losses = W.train(net, X, TT, args.steps, batch=args.batch, log=log)
+        torch.cuda.synchronize()
+        train_info[no] = {"seconds": time.time() - t0, "loss_initial": l0, "minibatch_losses": losses,
+                          "loss_final": net.gradients(X.data_ptr(), TT.data_ptr(), n_rows)}
+        nets[no] = net
+        if args.save:
+            np.save(f"{args.save}_out{no}.npy", net.get_params())
+    del X, T, T2
+
+    # ---- held-out samples: cold, learned warm (2 and 3 outputs), Kozeny
+    sts = W.build(ws_test)
+    ps = par(ws_test)
+    Xt = W.features(ws_test)
+    ru_c, st_c, sec_c, k_c = W.solve(sts, ps)
+    ru_2, st_2, sec_2, k_2 = W.solve(sts, ps, init=W.warm_init(nets[2], Xt, ws_test, ps))
+    ru_3, st_3, sec_3, k_3 = W.solve(sts, ps, init=W.warm_init(nets[3], Xt, ws_test, ps))
+    ru_k, st_k, sec_k, k_k = W.solve(sts, ps, init=W.kozeny_init(ws_test, ps))
+    # prediction error of the initial state against the converged cold state
+    Yd = torch.empty((Xt.shape[0], 3), dtype=torch.float32, device="cuda")
+    nets[3].forward(Xt.data_ptr(), Xt.shape[0], Yd.data_ptr())
+    torch.cuda.synchronize()
+    Y = Yd.cpu().numpy().astype(np.float64)
+    err_u, err_r, o = [], [], 0
+    for w, p in zip(ws_test, ps):
+        L = W.length_scale(w)
+        u = ru_c[o:o + w.n, 1:]
+        err_u.append(float(np.linalg.norm(W.velocity_scale(p.gx, p.tau, L) * Y[o:o + w.n, :2] - u) / np.linalg.norm(u)))
+        dr = ru_c[o:o + w.n, 0] - 1.0
+        pr = W.density_scale(p.gx, L) * Y[o:o + w.n, 2]
+        pr = pr - np.sum(pr * w.area) / np.sum(w.area)
+        err_r.append(float(np.linalg.norm(pr - dr) / np.linalg.norm(dr)))
+        o += w.n
+    # single-instance time to steady state (what one user run sees), first
+    # samples; the warm start's time includes features and inference
+    single = []
+    for i in range(min(args.single, len(ws_test))):
+        row = {}
+        for mode in ("cold", "warm"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx = mlbm.init(sts[i], ps[i])
+            if mode == "warm":
+                Xi = W.features([ws_test[i]])
+                L = W.length_scale(ws_test[i])
+                mlbm.warm_start(ctx, nets[3], Xi.data_ptr(), W.velocity_scale(args.g, 1.0, L), W.density_scale(args.g, L))
+            taken = mlbm.run_to_steady(ctx, W.TOL, W.WINDOW, 400_000, check=W.CHECK)
+            torch.cuda.synchronize()
+            row[mode + "_s"] = time.perf_counter() - t0
+            row[mode + "_steps"] = int(taken)
+            row[mode + "_k"] = mlbm.permeability(ctx)["k"]
+            del ctx
+        single.append(row)
+    rel = lambda a, b: np.abs(np.asarray(a) - np.asarray(b)) / np.abs(np.asarray(b))
+    mean_ratio = lambda a, b: float(np.mean(np.asarray(a, float) / np.asarray(b, float)))
+    out = {
+        "study": "warm", "train_samples": len(ws_train), "test_samples": len(ws_test),
+        "nodes_mean": float(np.mean([w.n for w in ws_train + ws_test])), "train_rows": int(n_rows),
+        "g": args.g, "tol": W.TOL, "window": W.WINDOW, "check_every": W.CHECK,
+        "train_steps_to_steady_mean": float(np.mean(train_steps)),
+        "mlp_steps": args.steps, "mlp_batch": args.batch, "target_variance": t_var,
+        "training": {f"outputs_{k}": v for k, v in train_info.items()},
+        "test_steps_mean": {"cold": float(np.mean(st_c)), "warm_velocity": float(np.mean(st_2)),
+                            "warm_velocity_density": float(np.mean(st_3)), "kozeny": float(np.mean(st_k))},
+        "test_steps_ratio_over_cold": {"warm_velocity": mean_ratio(st_2, st_c),
+                                       "warm_velocity_density": mean_ratio(st_3, st_c),
+                                       "kozeny": mean_ratio(st_k, st_c)},
+        "test_steps": {"cold": [int(v) for v in st_c], "warm_velocity": [int(v) for v in st_2],
+                       "warm_velocity_density": [int(v) for v in st_3]},
+        "test_batch_seconds": {"cold": sec_c, "warm_velocity": sec_2, "warm_velocity_density": sec_3,
+                               "kozeny": sec_k},
+        "k_rel_diff_vs_cold_max": {"warm_velocity": float(rel(k_2, k_c).max()),
+                                   "warm_velocity_density": float(rel(k_3, k_c).max()),
+                                   "kozeny": float(rel(k_k, k_c).max())},
+        "prediction_rel_l2_mean": {"velocity": float(np.mean(err_u)), "density": float(np.mean(err_r))},
+        "single_instance": single,
+        "seconds": {"generate": t_gen, "stencil_build": t_build, "train_solves": t_solve,
+                    "total": time.time() - t_all},
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
     b = sub.add_parser("batch")
     b.add_argument("--samples", type=int, default=64)
     b.add_argument("--steps", type=int, default=20)
+    w = sub.add_parser("warm")
+    w.add_argument("--train", type=int, default=512)
+    w.add_argument("--test", type=int, default=64)
+    w.add_argument("--nodes", type=int, default=200_000)
+    w.add_argument("--group", type=int, default=64)
+    w.add_argument("--g", type=float, default=1e-6)
+    w.add_argument("--steps", type=int, default=8000)
+    w.add_argument("--batch", type=int, default=65536)
+    w.add_argument("--seed", type=int, default=1)
+    w.add_argument("--single", type=int, default=4)
+    w.add_argument("--save", default="")
     args = ap.parse_args()
     if args.cmd == "batch":
         batch_study(args)
+    elif args.cmd == "warm":
+        warm_study(args)
 
 
 if __name__ == "__main__":
