@@ -83,6 +83,7 @@ __global__ void features_kernel(int64_t n, const double* __restrict__ xy, const 
     double d1 = INFINITY, d2 = INFINITY, nx = 0.0, ny = 0.0;
     double fp[4] = {G.ell, G.ell, G.ell, G.ell};  // +x, -x, +y, -y
     double S[kRadii] = {0.0, 0.0, 0.0, 0.0};
+    // the direction of a candidate is only formed when it becomes the nearest
     auto take = [&](double d, double ux, double uy) {
         if (d < d1) {
             d2 = d1;
@@ -93,6 +94,7 @@ __global__ void features_kernel(int64_t n, const double* __restrict__ xy, const 
             d2 = d;
         }
     };
+    const double reach = fmax(G.rho[kRadii - 1], G.ell);  // beyond it a disk cuts no circle and no ray
     for (int k = 0; k < G.n_disks; ++k) {
         const double cx = disks[3 * k], cy = disks[3 * k + 1], r = disks[3 * k + 2];
         double dx0 = x - cx, dy0 = y - cy;
@@ -102,11 +104,20 @@ __global__ void features_kernel(int64_t n, const double* __restrict__ xy, const 
             for (int iy = -G.pery; iy <= G.pery; ++iy) {
                 const double dx = dx0 + ix * G.lx, dy = dy0 + iy * G.ly;
                 const double dist = sqrt(dx * dx + dy * dy);
-                take(dist - r, dist > 0 ? dx / dist : 0.0, dist > 0 ? dy / dist : 0.0);
-                fp[0] = fmin(fp[0], ray_entry(dx, dy, r, 1.0));
-                fp[1] = fmin(fp[1], ray_entry(dx, dy, r, -1.0));
-                fp[2] = fmin(fp[2], ray_entry(dy, dx, r, 1.0));
-                fp[3] = fmin(fp[3], ray_entry(dy, dx, r, -1.0));
+                const double d = dist - r;
+                if (d < d2) {
+                    if (d < d1) take(d, dist > 0 ? dx / dist : 0.0, dist > 0 ? dy / dist : 0.0);
+                    else d2 = d;
+                }
+                if (d >= reach) continue;
+                if (fabs(dy) <= r) {
+                    fp[0] = fmin(fp[0], ray_entry(dx, dy, r, 1.0));
+                    fp[1] = fmin(fp[1], ray_entry(dx, dy, r, -1.0));
+                }
+                if (fabs(dx) <= r) {
+                    fp[2] = fmin(fp[2], ray_entry(dy, dx, r, 1.0));
+                    fp[3] = fmin(fp[3], ray_entry(dy, dx, r, -1.0));
+                }
 #pragma unroll
                 for (int j = 0; j < kRadii; ++j) S[j] += lens_area(dist, G.rho[j], r);
             }

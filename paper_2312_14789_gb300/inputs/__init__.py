@@ -188,7 +188,8 @@ def poiseuille_channel(nx: int = 40, ny: int = 50, jitter: float = 0.2, seed: in
 # --------------------------------------------------------------------------
 def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: float = 4.1,
            center_d: tuple = (2.0, 2.0), U0: float = 0.05, r_fine: float = 0.37, r_coarse: float = 0.74,
-           fine_band_d: float = 1.5, blend_to_d: float = 4.0, scale: float = 1.0) -> Workload:
+           fine_band_d: float = 1.5, blend_to_d: float = 4.0, scale: float = 1.0,
+           lattice_beyond_d: float | None = None) -> Workload:
     """Channel length_d*D x height_d*D with a solid cylinder of diameter D.
 
     Lengths are in units of the reference spacing h_ref=1, so D is the number
@@ -200,7 +201,16 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     the top and bottom, unit density everywhere.  No nodes closer than half
     the local radius to the cylinder surface apart from the wall nodes placed
     on it (arc spacing about 1.19 r_fine).  `scale` < 1 shrinks D and the
-    channel together for small test cases."""
+    channel together for small test cases.
+
+    lattice_beyond_d (hybrid node set, Sec. 3.1's regular bulk with scattered
+    refinement): nodes farther than lattice_beyond_d*D from the cylinder
+    surface sit on the square lattice of unit spacing that also carries the
+    side nodes (length and height are rounded to whole spacings); the
+    scattered refinement fills the rest, its radius blended from r_fine
+    (within min(fine_band_d, lattice_beyond_d/2)*D) to r_coarse at the
+    lattice.  Requires r_coarse > 1/sqrt(2), so
+    that no scattered node fits between lattice points."""
     D = D * scale
     lx, ly = length_d * D, height_d * D
     cx, cy, R = center_d[0] * D, center_d[1] * D, 0.5 * D
@@ -208,10 +218,19 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     nrx, nry = int(lx / 2) + 2, int(ly / 2) + 2
     gx, gy = np.meshgrid(np.linspace(0, lx, nrx), np.linspace(0, ly, nry), indexing="xy")
     dist = np.hypot(gx - cx, gy - cy) - R
+    if lattice_beyond_d is not None:
+        # the scattered refinement reaches the coarse radius where the lattice starts
+        blend_to_d = lattice_beyond_d
+        fine_band_d = min(fine_band_d, 0.5 * lattice_beyond_d)
     t = np.clip((dist - fine_band_d * D) / ((blend_to_d - fine_band_d) * D), 0.0, 1.0)
     rgrid = r_fine + t * (r_coarse - r_fine)
     # equilibrium nodes on the four sides
     hb = r_coarse * 1.19
+    if lattice_beyond_d is not None:
+        if r_coarse <= 0.5 ** 0.5:
+            raise ValueError("hybrid node sets need r_coarse > 1/sqrt(2)")
+        lx, ly = float(round(lx)), float(round(ly))
+        hb = 1.0
     nbx = int(round(lx / hb)); nby = int(round(ly / hb))
     xs = np.linspace(0.0, lx, nbx + 1)
     ys = np.linspace(0.0, ly, nby + 1)
@@ -226,9 +245,15 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     ph = np.random.default_rng(seed).uniform(0, 2 * np.pi)
     a = ph + 2 * np.pi * np.arange(m) / m
     surface = np.stack([cx + R * np.cos(a), cy + R * np.sin(a)], 1)
+    pre = [fixed, surface]
+    if lattice_beyond_d is not None:
+        gx_, gy_ = np.meshgrid(np.arange(1, int(lx)), np.arange(1, int(ly)), indexing="xy")
+        lat = np.stack([gx_.ravel(), gy_.ravel()], 1).astype(np.float64)
+        far = np.hypot(lat[:, 0] - cx, lat[:, 1] - cy) - R > lattice_beyond_d * D
+        pre.append(lat[far])
     pts = _sample((0.0, 0.0, lx, ly), (0, 0), rgrid, np.array([[cx, cy, R]]), 0.5,
-                  np.concatenate([fixed, surface], 0), seed,
-                  max_out=int(4 * lx * ly / r_fine ** 2) + len(fixed) + m + 1000)
+                  np.concatenate(pre, 0), seed,
+                  max_out=int(4 * lx * ly / r_fine ** 2) + sum(len(p) for p in pre) + 1000)
     n = len(pts)
     cls = np.zeros(n, np.uint8)
     cls[:nf] = EQ
@@ -246,9 +271,11 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     r_at = rgrid[fy.astype(int), fx.astype(int)]
     area = r_at ** 2
     area *= (lx * ly - np.pi * R * R) / area.sum()
-    return Workload(f"karman_D{D:g}_s{seed}", pts, cls, (0.0, 0.0, lx, ly), (OPEN,) * 4,
+    name = f"karman_D{D:g}_s{seed}" + ("" if lattice_beyond_d is None else f"_hybrid{lattice_beyond_d:g}")
+    return Workload(name, pts, cls, (0.0, 0.0, lx, ly), (OPEN,) * 4,
                     np.array([[cx, cy, R]]), eqv, area, 1.0,
-                    {"D": D, "U0": U0, "H": ly, "L": lx, "seed": seed, "n_eq": nf, "n_wall": m})
+                    {"D": D, "U0": U0, "H": ly, "L": lx, "seed": seed, "n_eq": nf, "n_wall": m,
+                     "lattice_beyond_d": lattice_beyond_d})
 
 
 # --------------------------------------------------------------------------

@@ -2,6 +2,7 @@
 
     python -m paper_2312_14789_gb300.studies batch [--samples 64] [--steps 20]
     python -m paper_2312_14789_gb300.studies warm [--train 512] [--test 64] [--nodes 200000]
+    python -m paper_2312_14789_gb300.studies hybrid [--steps 200000] [--lattice-d 1.0]
 
 batch: 64 porous samples (seeds 1000..1063) with node counts U(50k, 400k),
 porosity U(0.5, 0.85) and a mix of Darcy (s = 1) and inertial (s = 1/2, 1/4)
@@ -213,13 +214,22 @@ def warm_study(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ctx = mlbm.init(sts[i], ps[i])
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
             if mode == "warm":
                 Xi = W.features([ws_test[i]])
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
                 L = W.length_scale(ws_test[i])
                 mlbm.warm_start(ctx, nets[3], Xi.data_ptr(), W.velocity_scale(args.g, 1.0, L), W.density_scale(args.g, L))
+                torch.cuda.synchronize()
+                row["features_s"] = t2 - t1
+                row["inference_and_set_s"] = time.perf_counter() - t2
+            t3 = time.perf_counter()
             taken = mlbm.run_to_steady(ctx, W.TOL, W.WINDOW, 400_000, check=W.CHECK)
             torch.cuda.synchronize()
-            row[mode + "_s"] = time.perf_counter() - t0
+            row[mode + "_solve_s"] = time.perf_counter() - t3
+            row[mode + "_s"] = time.perf_counter() - t1
             row[mode + "_steps"] = int(taken)
             row[mode + "_k"] = mlbm.permeability(ctx)["k"]
             del ctx
@@ -253,6 +263,67 @@ def warm_study(args):
     print(json.dumps(out))
 
 
+def _strouhal(cl, every, d_lb, u0):
+    """St = f D / U0 from the mean spacing of upward zero crossings of
+    C_L - mean(C_L) (linear interpolation between samples)."""
+    c = np.asarray(cl, np.float64) - np.mean(cl)
+    i = np.nonzero((c[:-1] < 0) & (c[1:] >= 0))[0]
+    if len(i) < 3:
+        return float("nan")
+    tz = (i + (-c[i]) / (c[i + 1] - c[i])) * every
+    return float(d_lb / (np.mean(np.diff(tz)) * u0))
+
+
+def hybrid_study(args):
+    """Scattered vs hybrid (lattice bulk beyond --lattice-d diameters of the
+    cylinder surface, scattered refinement inside) vortex street at Re = 100,
+    s = 1/2: step throughput (autotuned, CUDA events, graphs), HBM fraction of
+    the algorithmic bytes, and the Strouhal number and mean drag after
+    --steps steps from rest."""
+    import torch
+    from paper_2312_14789_gb300 import inputs as I
+    from paper_2312_14789_gb300 import mlbm
+    sys.path.insert(0, ROOT)
+    import bench
+
+    re_, s_, u0, d = 100, 0.5, 0.05, 40.0
+    tau = 3.0 * u0 * (d / s_) / re_ + 0.5
+    peak = bench.peaks()[0]["hbm_gbs"]
+    out = {"study": "hybrid", "Re": re_, "s": s_, "tau": tau, "steps": args.steps}
+    for name, w in (("scattered", I.karman(seed=2)), ("hybrid", I.karman(seed=2, lattice_beyond_d=args.lattice_d))):
+        st = mlbm.build_stencils_for(w, K=16, s=s_, bb_mode=mlbm.BB_SIMPLE)
+        info = mlbm.stencils_info(st)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
+        variant, _ = mlbm.autotune(ctx, 10, flush_l2=True)
+        stream = torch.cuda.Stream()
+        mlbm.set_stream(ctx, stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            mlbm.step(ctx, 32)
+            e0.record(stream)
+            mlbm.step(ctx, 2048)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / 2048
+        alg = bench.algorithmic_bytes(info, 16)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
+        mlbm.set_kernel_variant(ctx, variant)
+        every = 50
+        cd, cl = np.empty(args.steps // every), np.empty(args.steps // every)
+        for i in range(len(cd)):
+            mlbm.step(ctx, every)
+            _, _, cd[i], cl[i] = mlbm.drag_lift(ctx, d, u0)
+        h = len(cd) // 2
+        out[name] = {"nodes": int(w.n), "n_wls": info["n_wls"], "n_lagrange": info["n_lagrange"],
+                     "n_eq": info["n_eq"], "variant": variant, "us_per_step": us,
+                     "mnups": w.n / us, "algorithmic_bytes_per_step": alg,
+                     "hbm_frac_of_measured_peak": alg / (us * 1e-6) / 1e9 / peak,
+                     "strouhal": _strouhal(cl[h:], every, d / s_, u0), "cd_mean": float(np.mean(cd[h:])),
+                     "cl_amplitude": float(np.ptp(cl[h:]) / 2)}
+    out["time_per_step_ratio_hybrid_over_scattered"] = out["hybrid"]["us_per_step"] / out["scattered"]["us_per_step"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -270,8 +341,13 @@ def main():
     w.add_argument("--seed", type=int, default=1)
     w.add_argument("--single", type=int, default=4)
     w.add_argument("--save", default="")
+    hb = sub.add_parser("hybrid")
+    hb.add_argument("--steps", type=int, default=200_000)
+    hb.add_argument("--lattice-d", type=float, default=1.0)
     args = ap.parse_args()
-    if args.cmd == "batch":
+    if args.cmd == "hybrid":
+        hybrid_study(args)
+    elif args.cmd == "batch":
         batch_study(args)
     elif args.cmd == "warm":
         warm_study(args)

@@ -69,7 +69,8 @@ def test_poiseuille_channel_2000_steps_matches_oracle():
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("case", ["lattice", "channel_halfway", "jittered", "karman_small", "porous_small"])
+@pytest.mark.parametrize("case", ["lattice", "channel_halfway", "jittered", "karman_small", "karman_hybrid_small",
+                                  "porous_small"])
 def test_bgk_steps_match_oracle_elementwise(case, variant):
     if case == "lattice":
         w, K, s, bb, tau, g = I.lattice(33, 17), 12, 1.0, 1, 0.7, (1e-5, -2e-6)
@@ -79,6 +80,8 @@ def test_bgk_steps_match_oracle_elementwise(case, variant):
         w, K, s, bb, tau, g = I.jittered_periodic(37, 29, 0.25, seed=4), 16, 0.8, 1, 0.75, (1e-5, 3e-6)
     elif case == "karman_small":
         w, K, s, bb, tau, g = I.karman(seed=2, scale=0.25), 16, 0.5, 0, 0.62, (0.0, 0.0)
+    elif case == "karman_hybrid_small":
+        w, K, s, bb, tau, g = I.karman(seed=2, scale=0.25, lattice_beyond_d=1.0), 16, 0.5, 0, 0.62, (0.0, 0.0)
     else:
         w, K, s, bb, tau, g = I.porous(seed=5, n_target=15000), 16, 0.5, 1, 0.8, (1e-5, 0.0)
     f0 = to_f32_state(random_populations(w.n, 11))
