@@ -70,9 +70,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(variant):
+ORDER_NAMES = ["hilbert", "morton", "rows", "input"]
+
+
+def measured_traffic(variant, order=0):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when it was taken on a different kernel source or variant."""
+    or None when it was taken on a different kernel source, variant or node
+    order."""
     try:
         txt = open(PROFILE).read()
     except OSError:
@@ -82,7 +86,8 @@ def measured_traffic(variant):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_hash") != kernel_source_hash() or vals.get("kernel_variant") != str(variant):
+    if vals.get("kernel_source_hash") != kernel_source_hash() or vals.get("kernel_variant") != str(variant) \
+            or vals.get("node_order", "hilbert") != ORDER_NAMES[order]:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -203,8 +208,10 @@ def run_ours(args, rank, world, local_rank):
     sts = [st_by_s[s] for _, s in CASES]
     params = [mlbm.Params(mlbm.MODEL_BGK, tau_of(re, s), 0.0, 0.0, 0.0) for re, s in CASES]
     infos = [mlbm.stencils_info(st) for st in sts]
+    # node order and kernel variant picked together by the library's autotuner
+    order, variant, tune_ms = mlbm.autotune_order(sts, params, 10)
     ctx = mlbm.batch_init(sts, params)
-    variant, tune_ms = mlbm.autotune(ctx, 10)
+    mlbm.set_kernel_variant(ctx, variant)
     stream = torch.cuda.Stream()
     mlbm.set_stream(ctx, stream.cuda_stream)
     n = ctx.n
@@ -254,11 +261,11 @@ def run_ours(args, rank, world, local_rank):
     bytes_launch = sum(algorithmic_bytes(i, 16) for i in infos)
     avg_ms = total_ms / args.steps
     achieved = bytes_launch / (avg_ms / 1e3) / 1e9
-    traffic = measured_traffic(variant)
+    traffic = measured_traffic(variant, order)
     cpu_val, cpu_threads, cpu_desc = oracle_sample_rate(w, 8192, 1, 10.0, 20000)
     cfg = dict(WORKLOAD, nodes_per_run=w.n, node_updates_per_step=n, parallelism=f"replicas x{world}",
                n_wls=int(sum(i["n_wls"] for i in infos)), n_eq=int(sum(i["n_eq"] for i in infos)),
-               n_links=int(sum(i["n_links"] for i in infos)), kernel_variant=variant,
+               n_links=int(sum(i["n_links"] for i in infos)), kernel_variant=variant, node_order=ORDER_NAMES[order],
                autotune_ms_per_step=tune_ms, cuda_graph_chunk=16)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

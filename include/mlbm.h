@@ -59,6 +59,9 @@ enum { MLBM_SIDE_PERIODIC = 0, MLBM_SIDE_SOLID = 1, MLBM_SIDE_OPEN = 2 };
 enum { MLBM_BB_SIMPLE = 0, MLBM_BB_INTERPOLATED = 1 };
 /* collision model */
 enum { MLBM_MODEL_BGK = 0, MLBM_MODEL_TAU1 = 1 };
+/* device node order: Hilbert curve (default), Morton (Z) curve, strips of
+   about 8 node spacings left to right, or the caller's order */
+enum { MLBM_ORDER_HILBERT = 0, MLBM_ORDER_MORTON = 1, MLBM_ORDER_ROWS = 2, MLBM_ORDER_INPUT = 3 };
 
 typedef struct mlbm_stencils mlbm_stencils;
 typedef struct mlbm_ctx mlbm_ctx;
@@ -128,6 +131,16 @@ typedef struct {
 } mlbm_stencil_info;
 
 mlbm_status mlbm_stencils_info(const mlbm_stencils* st, mlbm_stencil_info* info);
+
+/*
+ * Re-order the nodes of built stencils (the order the device arrays, and so
+ * the neighbour gathers, follow): MLBM_ORDER_*.  Host-only; contexts made
+ * afterwards use the new order (results in the caller's order are the same
+ * up to FP32 summation order).  The paper has no counterpart (its nodes are
+ * visited in input order by one CPU thread).  Errors: MLBM_E_INVALID.
+ */
+mlbm_status mlbm_stencils_set_order(mlbm_stencils* st, int order);
+int mlbm_stencils_order(const mlbm_stencils* st);
 
 /*
  * Copy the stencil data out in the caller's node order (for inspection and
@@ -307,6 +320,20 @@ mlbm_status mlbm_batch_run_to_steady(mlbm_ctx* ctx, double tol, int64_t window, 
                                      int64_t* steps_taken);
 mlbm_status mlbm_batch_run_to_steady_ex(mlbm_ctx* ctx, double tol, int64_t window, int64_t check,
                                         int64_t max_steps, int64_t* steps_taken);
+
+/*
+ * Autotune the node order together with the kernel variant: for every
+ * MLBM_ORDER_* the stencils of all n_samples samples are re-ordered, a
+ * context is made from them (mlbm_init for one sample, mlbm_batch_init
+ * otherwise, with params[]), its variants are timed (mlbm_autotune_ex with
+ * steps_per_variant and flush_l2) and the context is released; the stencils
+ * are left in the fastest order.  best_order, best_variant and best_ms
+ * (nullable) receive the winner.  Needs device memory for one context at a
+ * time.  Errors: as mlbm_init / mlbm_batch_init / mlbm_autotune_ex.
+ */
+mlbm_status mlbm_autotune_order(mlbm_stencils* const* stencils, const mlbm_params* params, int n_samples,
+                                int steps_per_variant, int flush_l2, int* best_order, int* best_variant,
+                                double* best_ms);
 
 /* mlbm_step replays chunks of 16 launches from captured CUDA graphs (one per
    starting buffer, re-captured when the variant or stream changes); enable = 0

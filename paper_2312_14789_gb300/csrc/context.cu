@@ -61,7 +61,7 @@ struct mlbm_ctx {
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = -1.0;
-    int variant = 4;
+    int variant = 12;
     int* err = nullptr;  // device error word of the bounded waits
     dev::Stencil S{};
     dev::Collide C{};
@@ -272,7 +272,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     MLBM_TRY(dalloc(c, &c->seg_out, 6 * (c->seg_off.size() - 1)));
     MLBM_TRY(dalloc(c, &c->err, 1));
     MLBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
-    if (!tma_supported(Kq)) c->variant = 1;
+    if (!tma_supported(Kq)) c->variant = 1;  // variants >= 4 exist for K in {12, 16, 24, 32}
     MLBM_TRY(upload(c, c->idx, hidx.data(), hidx.size() * 4));
     MLBM_TRY(upload(c, c->M, hM.data(), hM.size() * 4));
     MLBM_TRY(upload(c, c->meta, hmeta.data(), np));
@@ -1066,6 +1066,38 @@ mlbm_status mlbm_warm_start(mlbm_ctx* c, mlbm_mlp* m, const float* X, const doub
     if (n_cold)
         for (int i = 0; i < ns; ++i) *n_cold += hflag[i] != 0;
     c->steps = 0;
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_autotune_order(mlbm_stencils* const* sts, const mlbm_params* params, int n_samples,
+                                int steps_per_variant, int flush_l2, int* best_order, int* best_variant,
+                                double* best_ms) {
+    clear_error();
+    if (!sts || !params || n_samples < 1 || steps_per_variant < 1)
+        return set_error(MLBM_E_INVALID, "autotune_order: bad arguments");
+    int bo = -1, bv = -1;
+    double bt = 1e300;
+    for (int order = MLBM_ORDER_HILBERT; order <= MLBM_ORDER_INPUT; ++order) {
+        for (int i = 0; i < n_samples; ++i) MLBM_TRY(mlbm_stencils_set_order(sts[i], order));
+        mlbm_ctx* c = nullptr;
+        mlbm_status st = n_samples == 1 ? mlbm_init(&c, sts[0], &params[0], nullptr, nullptr)
+                                        : mlbm_batch_init(&c, sts, params, n_samples);
+        if (st != MLBM_OK) return st;
+        double ms = 0.0;
+        st = mlbm_autotune_ex(c, steps_per_variant, flush_l2, &ms);
+        const int v = c->variant;
+        mlbm_destroy(c);
+        if (st != MLBM_OK) return st;
+        if (ms < bt) {
+            bt = ms;
+            bo = order;
+            bv = v;
+        }
+    }
+    for (int i = 0; i < n_samples; ++i) MLBM_TRY(mlbm_stencils_set_order(sts[i], bo));
+    if (best_order) *best_order = bo;
+    if (best_variant) *best_variant = bv;
+    if (best_ms) *best_ms = bt;
     return MLBM_OK;
 }
 

@@ -40,6 +40,10 @@ struct HostStencils {
     std::vector<double> area;      // [n]
     // batches: streaming distance of each node (empty: s for all)
     std::vector<double> s_node;
+    // node positions in the caller's order and the box, for re-ordering
+    std::vector<double> xy;
+    double bx0 = 0, by0 = 0, blx = 1, bly = 1;
+    int order = 0;  // MLBM_ORDER_*
     mlbm_stencil_info info{};
 };
 

@@ -332,6 +332,48 @@ int links_of(double x, double y, double s, const Box& b, const double* disks, in
     return 0;
 }
 
+// Morton (Z-order) index: the bits of x and y interleaved.
+uint64_t morton_index(uint32_t x, uint32_t y) {
+    uint64_t d = 0;
+    for (int b = 0; b < 32; ++b) d |= ((uint64_t)((x >> b) & 1u) << (2 * b)) | ((uint64_t)((y >> b) & 1u) << (2 * b + 1));
+    return d;
+}
+
+uint64_t hilbert_index(uint32_t x, uint32_t y, int order);
+
+// Position -> caller id for a node order (MLBM_ORDER_*).  Keys come from the
+// positions scaled to [0, 2^16) over the box; ties keep the caller's order.
+// Rows: strips of height ~ the mean node spacing times 8, left to right in
+// each strip.
+std::vector<int64_t> order_nodes(const std::vector<double>& xy, double x0, double y0, double lx, double ly,
+                                 int order) {
+    const int64_t n = (int64_t)(xy.size() / 2);
+    std::vector<int64_t> perm(n);
+    std::iota(perm.begin(), perm.end(), 0);
+    if (order == MLBM_ORDER_INPUT) return perm;
+    std::vector<uint64_t> key(n);
+    const int bits = 16;
+    const double scale = (double)((1u << bits) - 1);
+    const double strip = 8.0 * std::sqrt(lx * ly / std::max<int64_t>(n, 1));
+    const int64_t n_strips = std::max<int64_t>(1, (int64_t)std::ceil(ly / strip));
+    for (int64_t i = 0; i < n; ++i) {
+        double u = (xy[2 * i] - x0) / lx, v = (xy[2 * i + 1] - y0) / ly;
+        u = std::min(1.0, std::max(0.0, u));
+        v = std::min(1.0, std::max(0.0, v));
+        const uint32_t ux = (uint32_t)(u * scale), vy = (uint32_t)(v * scale);
+        if (order == MLBM_ORDER_MORTON) {
+            key[i] = morton_index(ux, vy);
+        } else if (order == MLBM_ORDER_ROWS) {
+            const int64_t row = std::min<int64_t>(n_strips - 1, (int64_t)(v * n_strips));
+            key[i] = ((uint64_t)row << 32) | ux;
+        } else {
+            key[i] = hilbert_index(ux, vy, bits);
+        }
+    }
+    std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t c) { return key[a] < key[c]; });
+    return perm;
+}
+
 // Hilbert index of (x, y) in [0, 2^order)^2.
 uint64_t hilbert_index(uint32_t x, uint32_t y, int order) {
     uint64_t d = 0;
@@ -455,19 +497,14 @@ extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_g
                          "build_stencils: degenerate least-squares stencil at node " + std::to_string(bad_node));
     }
 
-    // Hilbert order
-    std::vector<uint64_t> key(n);
-    const int order = 16;
-    const double scale = (double)((1u << order) - 1);
-    for (int64_t i = 0; i < n; ++i) {
-        double u = (xy[2 * i] - b.x0) / b.lx, v = (xy[2 * i + 1] - b.y0) / b.ly;
-        u = std::min(1.0, std::max(0.0, u));
-        v = std::min(1.0, std::max(0.0, v));
-        key[i] = hilbert_index((uint32_t)(u * scale), (uint32_t)(v * scale), order);
-    }
-    H.perm.resize(n);
-    std::iota(H.perm.begin(), H.perm.end(), 0);
-    std::stable_sort(H.perm.begin(), H.perm.end(), [&](int64_t a, int64_t c) { return key[a] < key[c]; });
+    // node order (Hilbert by default)
+    H.xy.assign(xy, xy + 2 * (size_t)n);
+    H.bx0 = b.x0;
+    H.by0 = b.y0;
+    H.blx = b.lx;
+    H.bly = b.ly;
+    H.order = MLBM_ORDER_HILBERT;
+    H.perm = order_nodes(H.xy, b.x0, b.y0, b.lx, b.ly, H.order);
     H.inv.resize(n);
     for (int64_t p = 0; p < n; ++p) H.inv[H.perm[p]] = p;
 
@@ -538,3 +575,50 @@ extern "C" mlbm_status mlbm_stencils_export(const mlbm_stencils* st, int64_t* id
     }
     return MLBM_OK;
 }
+
+extern "C" mlbm_status mlbm_stencils_set_order(mlbm_stencils* st, int order) {
+    clear_error();
+    if (!st || order < MLBM_ORDER_HILBERT || order > MLBM_ORDER_INPUT)
+        return set_error(MLBM_E_INVALID, "stencils_set_order: bad arguments");
+    HostStencils& H = st->h;
+    if (H.order == order) return MLBM_OK;
+    if ((int64_t)H.xy.size() != 2 * H.n)
+        return set_error(MLBM_E_INVALID, "stencils_set_order: these stencils carry no node positions");
+    const int64_t n = H.n;
+    const int K = H.K;
+    std::vector<int64_t> perm = order_nodes(H.xy, H.bx0, H.by0, H.blx, H.bly, order);
+    std::vector<int64_t> inv(n);
+    for (int64_t p = 0; p < n; ++p) inv[perm[p]] = p;
+    // new position q takes what sat at old position H.inv[perm[q]]; neighbour
+    // positions are mapped through the caller ids
+    auto move = [&](auto& v, size_t w) {
+        auto old = v;
+        for (int64_t q = 0; q < n; ++q) {
+            const int64_t o = H.inv[perm[q]];
+            std::copy(old.begin() + (size_t)o * w, old.begin() + (size_t)(o + 1) * w, v.begin() + (size_t)q * w);
+        }
+    };
+    {
+        std::vector<int32_t> old = H.idx;
+        for (int64_t q = 0; q < n; ++q) {
+            const int64_t o = H.inv[perm[q]];
+            for (int j = 0; j < K; ++j) H.idx[(size_t)q * K + j] = (int32_t)inv[H.perm[old[(size_t)o * K + j]]];
+        }
+    }
+    move(H.M, (size_t)6 * K);
+    move(H.kind, 1);
+    move(H.center, 1);
+    move(H.lag_h, 1);
+    move(H.lag_slot, 9);
+    move(H.link_mask, 1);
+    move(H.q, 9);
+    move(H.eqv, 3);
+    move(H.area, 1);
+    if (!H.s_node.empty()) move(H.s_node, 1);
+    H.perm = std::move(perm);
+    H.inv = std::move(inv);
+    H.order = order;
+    return MLBM_OK;
+}
+
+extern "C" int mlbm_stencils_order(const mlbm_stencils* st) { return st ? st->h.order : -1; }

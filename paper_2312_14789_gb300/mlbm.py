@@ -16,6 +16,7 @@ import numpy as np
 from . import _build
 
 MODEL_BGK, MODEL_TAU1 = 0, 1
+ORDER_HILBERT, ORDER_MORTON, ORDER_ROWS, ORDER_INPUT = 0, 1, 2, 3
 BB_SIMPLE, BB_INTERPOLATED = 0, 1
 NODE_FLUID, NODE_WALL, NODE_EQ = 0, 1, 2
 SIDE_PERIODIC, SIDE_SOLID, SIDE_OPEN = 0, 1, 2
@@ -65,6 +66,9 @@ def lib():
                 "mlbm_build_stencils": (st, [_vp, _vp, _i32, _dbl, _dbl, _i32, _i32, _vp]),
                 "mlbm_stencils_free": (None, [_vp]),
                 "mlbm_stencils_info": (st, [_vp, _vp]),
+                "mlbm_stencils_set_order": (st, [_vp, _i32]),
+                "mlbm_stencils_order": (_i32, [_vp]),
+                "mlbm_autotune_order": (st, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
                 "mlbm_stencils_export": (st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
                 "mlbm_init": (st, [_vp, _vp, _vp, _vp, _vp]),
                 "mlbm_destroy": (None, [_vp]),
@@ -178,6 +182,26 @@ def stencils_info(st: Stencils) -> dict:
     info = _Info()
     _check(lib().mlbm_stencils_info(st.handle, ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in _Info._fields_}
+
+
+def stencils_set_order(st: Stencils, order: int):
+    _check(lib().mlbm_stencils_set_order(st.handle, int(order)))
+
+
+def stencils_order(st: Stencils) -> int:
+    return int(lib().mlbm_stencils_order(st.handle))
+
+
+def autotune_order(stencils: list, params: list, steps_per_variant: int = 10, flush_l2: bool = False) -> tuple:
+    """Pick the node order and kernel variant together; leaves the stencils in
+    the winning order.  Returns (order, variant, ms per step)."""
+    arr = (_vp * len(stencils))(*[s.handle for s in stencils])
+    par = (_Params * len(params))(*[_Params(int(p.model), float(p.tau), float(p.tau_minus), float(p.gx), float(p.gy))
+                                    for p in params])
+    o, v, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().mlbm_autotune_order(arr, par, len(stencils), int(steps_per_variant), int(bool(flush_l2)),
+                                     ctypes.byref(o), ctypes.byref(v), ctypes.byref(ms)))
+    return o.value, v.value, ms.value
 
 
 def stencils_export(st: Stencils) -> dict:

@@ -85,8 +85,18 @@ def batch_study(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3
 
+    # node order: time every order (stencils re-ordered, variants tuned), then
+    # let the library's order autotuner pick
+    order_ms = {}
+    for o, name in enumerate(["hilbert", "morton", "rows", "input"]):
+        for st in sts:
+            mlbm.stencils_set_order(st, o)
+        b = mlbm.batch_init(sts, ps)
+        _, order_ms[name] = mlbm.autotune(b, 5)
+        del b
+    order, variant, _ = mlbm.autotune_order(sts, ps, 5)
     batch = mlbm.batch_init(sts, ps)
-    variant, tune_ms = mlbm.autotune(batch, 5)
+    mlbm.set_kernel_variant(batch, variant)
     t_batch = timed(batch, args.steps)
     k_batch = mlbm.batch_permeability(batch)["k"]
     del batch
@@ -105,7 +115,8 @@ def batch_study(args):
         "study": "batch", "samples": args.samples, "nodes_total": n_tot, "steps": args.steps,
         "batched_mnups": n_tot * args.steps / t_batch / 1e6,
         "sequential_mnups": n_tot * args.steps / t_seq / 1e6,
-        "speedup": t_seq / t_batch, "batch_variant": variant,
+        "speedup": t_seq / t_batch, "batch_variant": variant, "batch_node_order": order,
+        "autotune_ms_per_step_by_order": order_ms,
         "single_variants": sorted(set(variants)),
         "permeability_max_rel_diff_batch_vs_single": float(np.max(np.abs(k_batch - k_single) / np.abs(k_single))),
         "porosity_range": [float(min(w.meta["porosity"] for w in ws)), float(max(w.meta["porosity"] for w in ws))],

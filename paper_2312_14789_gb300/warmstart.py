@@ -86,6 +86,7 @@ def solve(sts, params, tol=TOL, window=WINDOW, max_steps=400_000, init=None, che
     permeability per sample)."""
     import torch
     ctx = mlbm.batch_init(sts, params)
+    mlbm.autotune(ctx, 5)          # keeps the state
     if init is not None:
         init(ctx)
     torch.cuda.synchronize()

@@ -99,3 +99,25 @@ def test_builder_errors():
     with pytest.raises(mlbm.MlbmError) as e:
         mlbm.build_stencils(xy, np.zeros(64, np.uint8), (0, 0, 8, 8), (0, 0, 0, 0), disks=[[3.0, 3.0, 1.5]], K=12)
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 0])
+def test_reordering_keeps_the_stencils(order):
+    """Re-ordering the device node order changes no stencil datum in the
+    caller's order (bit-exact), and the orders differ as positions."""
+    w = I.karman(seed=2, scale=0.25, lattice_beyond_d=1.0)
+    st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=0)
+    ref = mlbm.stencils_export(st)
+    assert mlbm.stencils_order(st) == 0
+    mlbm.stencils_set_order(st, order)
+    assert mlbm.stencils_order(st) == order
+    got = mlbm.stencils_export(st)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+    # back to Hilbert and again
+    mlbm.stencils_set_order(st, 0)
+    got = mlbm.stencils_export(st)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+    with pytest.raises(mlbm.MlbmError):
+        mlbm.stencils_set_order(st, 7)

@@ -84,3 +84,27 @@ def test_graph_replay_matches_direct_launches():
         mlbm.step(b, n)
     assert mlbm.step_count(a) == mlbm.step_count(b) == 104
     assert np.array_equal(mlbm.get_fields(a), mlbm.get_fields(b))
+
+
+def test_node_order_autotuner():
+    """The order autotuner tries every node order, leaves the stencils in the
+    fastest, and the physics does not depend on the order (FP32 summation
+    order only)."""
+    from paper_2312_14789_gb300 import inputs as I
+    ws = [I.porous(seed=s, n_target=8000, porosity=0.7) for s in (31, 32)]
+    sts = [mlbm.build_stencils_for(w, K=16, s=1.0, bb_mode=mlbm.BB_INTERPOLATED) for w in ws]
+    ps = [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, 1e-5, 0.0)] * 2
+    ref = mlbm.batch_init(sts, ps)
+    mlbm.step(ref, 50)
+    ru_ref = mlbm.get_fields(ref)
+    order, variant, ms = mlbm.autotune_order(sts, ps, 3)
+    assert order in (0, 1, 2, 3) and ms > 0
+    assert all(mlbm.stencils_order(s) == order for s in sts)
+    for o in (1, 2, 3):
+        for s in sts:
+            mlbm.stencils_set_order(s, o)
+        c = mlbm.batch_init(sts, ps)
+        mlbm.step(c, 50)
+        ru = mlbm.get_fields(c)
+        assert np.abs(ru[:, 1:] - ru_ref[:, 1:]).max() <= 1e-5 * np.abs(ru_ref[:, 1:]).max() + 1e-12
+        assert np.abs(ru[:, 0] - ru_ref[:, 0]).max() <= 1e-6
