@@ -449,8 +449,9 @@ mlbm_status mlbm_mlp_train_device(mlbm_mlp* m, const float* X, const float* T, i
  *   1,2 unit vector from that surface point to the node (0 if no solid)
  *   3   clamp(d2 / L, 0, 4)   d2 = distance to the second nearest solid object
  *   4..7 free paths along +x, -x, +y, -y (distance to the first solid along
- *        the ray, at most ell) over L; a ray starting on a surface and
- *        pointing out of the solid does not meet it
+ *        the ray, at most ell) over L; a ray meets a disk where it enters
+ *        it, and an entry behind the start by more than 1e-4 r (a node on
+ *        the surface looking out of the solid) does not count
  *   8   clamp(f(+y) f(-y) / L^2, 0, 16), 9  clamp((f(+y) + f(-y)) / L, 0, 8)
  *   10..13 local porosity 1 - (solid area within distance rho_j of the node)
  *         / (pi rho_j^2), rho_j = min(c_j L, half the smaller box extent),
@@ -459,7 +460,11 @@ mlbm_status mlbm_mlp_train_device(mlbm_mlp* m, const float* X, const float* T, i
  *         circular segments;
  *   14  porosity of the box, 1 - sum(pi r^2) / box area
  *   15  4 (y - y0) (y1 - y) / (y1 - y0)^2 (position across the box)
- * With no solid object d1 = d2 = 4 L.  Computed in FP64 on the device.
+ * With no solid object d1 = d2 = 4 L.  Computed on the device with the
+ * positions and displacements in FP64 and the geometry in FP32 (the features
+ * feed a BF16 network): within about 1e-5 of an FP64 evaluation, except that
+ * the nearest of two nearly equidistant objects, or a ray grazing a disk, may
+ * be decided the other way.
  * Inputs are host arrays (copied to the device inside); synchronous.
  * Errors: MLBM_E_INVALID, MLBM_E_CUDA.
  */

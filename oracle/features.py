@@ -20,7 +20,7 @@ Objects: every disk with the images ix, iy in {-1, 0, 1} (around the
 minimum-image displacement) along each axis whose two sides are periodic,
 then the solid sides (left, right, bottom, top).  With no object d1 = d2 =
 4L.  Ties: the first object in that order gives the direction.  A ray meets
-a disk where it enters it; an entry behind the start by more than 1e-6 (a
+a disk where it enters it; an entry behind the start by more than 1e-4 r (a
 node on the surface looking out of the solid) does not count.
 
 The solid area inside a circle is the sum over objects of the closed-form
@@ -78,7 +78,7 @@ def _ray_hits(along, across, r):
     (along = node - centre on the ray axis); inf where the ray misses."""
     half = np.sqrt(np.maximum(r * r - across ** 2, 0.0))      # half-chord at that offset
     entry = -along - half                                     # centre position minus half-chord
-    ok = (np.abs(across) <= r) & (entry >= -1e-6)
+    ok = (np.abs(across) <= r) & (entry >= -1e-4 * r)
     return np.where(ok, np.maximum(entry, 0.0), np.inf)
 
 

@@ -1,4 +1,5 @@
-// Geometry features of the learned warm start (one thread per node, FP64)
+// Geometry features of the learned warm start (one thread per node; FP64
+// positions and displacements, FP32 geometry)
 // and the kernels that turn a network prediction into an initial state.
 //
 // Features (16 per node, L = length scale, ell = min(8 L, min(Lx, Ly) / 2)):
@@ -20,7 +21,8 @@
 // images ix = -1, 0, 1 outer and iy inner around the minimum image, then the
 // solid sides left, right, bottom, top); the first strictly nearer object
 // sets the direction.  A ray meets a disk when its entry point lies at
-// t >= -1e-6 (nodes on a surface looking outward see no hit).
+// t >= -1e-4 r (a node on the surface looking into the disk sees it at 0,
+// looking outward it sees no hit).
 #include <cmath>
 #include <string>
 #include <vector>
@@ -32,26 +34,27 @@ namespace mlbm {
 namespace dev {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr float kPif = 3.14159265358979f;
 
 // area of the intersection of two circles of radii a and b, centres d apart
-__device__ double lens_area(double d, double a, double b) {
-    if (d >= a + b) return 0.0;
-    if (d <= fabs(a - b)) {
-        const double m = fmin(a, b);
-        return kPi * m * m;
+__device__ float lens_area(float d, float a, float b) {
+    if (d >= a + b) return 0.f;
+    if (d <= fabsf(a - b)) {
+        const float m = fminf(a, b);
+        return kPif * m * m;
     }
-    const double ca = fmin(1.0, fmax(-1.0, (d * d + a * a - b * b) / (2.0 * d * a)));
-    const double cb = fmin(1.0, fmax(-1.0, (d * d + b * b - a * a) / (2.0 * d * b)));
-    const double k = fmax(0.0, (-d + a + b) * (d + a - b) * (d - a + b) * (d + a + b));
-    return a * a * acos(ca) + b * b * acos(cb) - 0.5 * sqrt(k);
+    const float ca = fminf(1.f, fmaxf(-1.f, (d * d + a * a - b * b) / (2.f * d * a)));
+    const float cb = fminf(1.f, fmaxf(-1.f, (d * d + b * b - a * a) / (2.f * d * b)));
+    const float k = fmaxf(0.f, (-d + a + b) * (d + a - b) * (d - a + b) * (d + a + b));
+    return a * a * acosf(ca) + b * b * acosf(cb) - 0.5f * sqrtf(k);
 }
 
 // area of the part of a circle of radius a beyond a line at signed distance h
 // from its centre
-__device__ double segment_area(double h, double a) {
-    if (h >= a) return 0.0;
-    if (h <= -a) return kPi * a * a;
-    return a * a * acos(h / a) - h * sqrt(a * a - h * h);
+__device__ float segment_area(float h, float a) {
+    if (h >= a) return 0.f;
+    if (h <= -a) return kPif * a * a;
+    return a * a * acosf(h / a) - h * sqrtf((a - h) * (a + h));
 }
 
 constexpr int kRadii = 4;
@@ -61,30 +64,33 @@ struct FeatGeo {
     int perx, pery;
     int solid[4];
     int n_disks;
-    double L, ell;
-    double rho[kRadii];
-    double porosity;
+    float L, ell;
+    float rho[kRadii];
+    float porosity;
 };
 
 // entry distance of a ray along +a (sign = +1) or -a (sign = -1) into a disk,
-// da = node - centre along the ray axis, db across it; INFINITY when missed
-__device__ __forceinline__ double ray_entry(double da, double db, double r, double sign) {
-    const double disc = r * r - db * db;
-    if (disc < 0.0) return INFINITY;
-    const double t = -sign * da - sqrt(disc);
-    return t >= -1e-6 ? fmax(t, 0.0) : INFINITY;
+// da = node - centre along the ray axis, db across it (|db| <= r); the
+// half-chord is formed as a product of sums, which keeps its accuracy at
+// grazing incidence; INFINITY when the entry lies behind the start (by more
+// than 1e-4 r, which absorbs the rounding of a start on the surface)
+__device__ __forceinline__ float ray_entry(float da, float db, float r, float sign) {
+    const float adb = fabsf(db);
+    const float t = -sign * da - sqrtf((r - adb) * (r + adb));
+    return t >= -1e-4f * r ? fmaxf(t, 0.f) : INFINITY;
 }
 
+// Displacements come from the FP64 positions (minimum image in FP64), the
+// rest is FP32: the features feed a BF16 network.
 __global__ void features_kernel(int64_t n, const double* __restrict__ xy, const double* __restrict__ disks,
                                 FeatGeo G, float* __restrict__ X) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double x = xy[2 * i], y = xy[2 * i + 1];
-    double d1 = INFINITY, d2 = INFINITY, nx = 0.0, ny = 0.0;
-    double fp[4] = {G.ell, G.ell, G.ell, G.ell};  // +x, -x, +y, -y
-    double S[kRadii] = {0.0, 0.0, 0.0, 0.0};
-    // the direction of a candidate is only formed when it becomes the nearest
-    auto take = [&](double d, double ux, double uy) {
+    float d1 = INFINITY, d2 = INFINITY, nx = 0.f, ny = 0.f;
+    float fp[4] = {G.ell, G.ell, G.ell, G.ell};  // +x, -x, +y, -y
+    float S[kRadii] = {0.f, 0.f, 0.f, 0.f};
+    auto take = [&](float d, float ux, float uy) {
         if (d < d1) {
             d2 = d1;
             d1 = d;
@@ -94,59 +100,61 @@ __global__ void features_kernel(int64_t n, const double* __restrict__ xy, const 
             d2 = d;
         }
     };
-    const double reach = fmax(G.rho[kRadii - 1], G.ell);  // beyond it a disk cuts no circle and no ray
+    const float reach = fmaxf(G.rho[kRadii - 1], G.ell);  // beyond it a disk cuts no circle and no ray
+    const float lxf = (float)G.lx, lyf = (float)G.ly;
     for (int k = 0; k < G.n_disks; ++k) {
-        const double cx = disks[3 * k], cy = disks[3 * k + 1], r = disks[3 * k + 2];
+        const double cx = disks[3 * k], cy = disks[3 * k + 1];
+        const float r = (float)disks[3 * k + 2];
         double dx0 = x - cx, dy0 = y - cy;
         if (G.perx) dx0 -= G.lx * rint(dx0 / G.lx);
         if (G.pery) dy0 -= G.ly * rint(dy0 / G.ly);
         for (int ix = -G.perx; ix <= G.perx; ++ix)
             for (int iy = -G.pery; iy <= G.pery; ++iy) {
-                const double dx = dx0 + ix * G.lx, dy = dy0 + iy * G.ly;
-                const double dist = sqrt(dx * dx + dy * dy);
-                const double d = dist - r;
+                const float dx = (float)dx0 + ix * lxf, dy = (float)dy0 + iy * lyf;
+                const float dist = sqrtf(dx * dx + dy * dy);
+                const float d = dist - r;
                 if (d < d2) {
-                    if (d < d1) take(d, dist > 0 ? dx / dist : 0.0, dist > 0 ? dy / dist : 0.0);
+                    if (d < d1) take(d, dist > 0.f ? dx / dist : 0.f, dist > 0.f ? dy / dist : 0.f);
                     else d2 = d;
                 }
                 if (d >= reach) continue;
-                if (fabs(dy) <= r) {
-                    fp[0] = fmin(fp[0], ray_entry(dx, dy, r, 1.0));
-                    fp[1] = fmin(fp[1], ray_entry(dx, dy, r, -1.0));
+                if (fabsf(dy) <= r) {
+                    fp[0] = fminf(fp[0], ray_entry(dx, dy, r, 1.f));
+                    fp[1] = fminf(fp[1], ray_entry(dx, dy, r, -1.f));
                 }
-                if (fabs(dx) <= r) {
-                    fp[2] = fmin(fp[2], ray_entry(dy, dx, r, 1.0));
-                    fp[3] = fmin(fp[3], ray_entry(dy, dx, r, -1.0));
+                if (fabsf(dx) <= r) {
+                    fp[2] = fminf(fp[2], ray_entry(dy, dx, r, 1.f));
+                    fp[3] = fminf(fp[3], ray_entry(dy, dx, r, -1.f));
                 }
 #pragma unroll
                 for (int j = 0; j < kRadii; ++j) S[j] += lens_area(dist, G.rho[j], r);
             }
     }
-    const double h[4] = {x - G.x0, G.x0 + G.lx - x, y - G.y0, G.y0 + G.ly - y};
-    const double wn[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+    const float h[4] = {(float)(x - G.x0), (float)(G.x0 + G.lx - x), (float)(y - G.y0), (float)(G.y0 + G.ly - y)};
+    const float wn[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
     const int ray_of_side[4] = {1, 0, 3, 2};  // the -x ray meets the left side, ...
     for (int sd = 0; sd < 4; ++sd) {
         if (!G.solid[sd]) continue;
         take(h[sd], wn[sd][0], wn[sd][1]);
-        fp[ray_of_side[sd]] = fmin(fp[ray_of_side[sd]], fmax(h[sd], 0.0));
+        fp[ray_of_side[sd]] = fminf(fp[ray_of_side[sd]], fmaxf(h[sd], 0.f));
 #pragma unroll
         for (int j = 0; j < kRadii; ++j) S[j] += segment_area(h[sd], G.rho[j]);
     }
-    if (!(d1 < INFINITY)) d1 = 4.0 * G.L;
-    if (!(d2 < INFINITY)) d2 = 4.0 * G.L;
-    const double a = d1 / G.L, b = d2 / G.L;
+    if (!(d1 < INFINITY)) d1 = 4.f * G.L;
+    if (!(d2 < INFINITY)) d2 = 4.f * G.L;
+    const float a = d1 / G.L, b = d2 / G.L;
     float* o = X + 16 * i;
-    o[0] = (float)fmin(fmax(a, 0.0), 4.0);
-    o[1] = (float)nx;
-    o[2] = (float)ny;
-    o[3] = (float)fmin(fmax(b, 0.0), 4.0);
+    o[0] = fminf(fmaxf(a, 0.f), 4.f);
+    o[1] = nx;
+    o[2] = ny;
+    o[3] = fminf(fmaxf(b, 0.f), 4.f);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) o[4 + j] = (float)(fp[j] / G.L);
-    o[8] = (float)fmin(fp[2] * fp[3] / (G.L * G.L), 16.0);
-    o[9] = (float)fmin((fp[2] + fp[3]) / G.L, 8.0);
+    for (int j = 0; j < 4; ++j) o[4 + j] = fp[j] / G.L;
+    o[8] = fminf(fp[2] * fp[3] / (G.L * G.L), 16.f);
+    o[9] = fminf((fp[2] + fp[3]) / G.L, 8.f);
 #pragma unroll
-    for (int j = 0; j < kRadii; ++j) o[10 + j] = (float)(1.0 - S[j] / (kPi * G.rho[j] * G.rho[j]));
-    o[14] = (float)G.porosity;
+    for (int j = 0; j < kRadii; ++j) o[10 + j] = 1.f - S[j] / (kPif * G.rho[j] * G.rho[j]);
+    o[14] = G.porosity;
     const double yy = y - G.y0;
     o[15] = (float)(4.0 * yy * (G.ly - yy) / (G.ly * G.ly));
 }
@@ -260,13 +268,13 @@ extern "C" mlbm_status mlbm_features_device(const mlbm_nodes* nodes, const mlbm_
     G.pery = geo->side[2] == MLBM_SIDE_PERIODIC && geo->side[3] == MLBM_SIDE_PERIODIC;
     for (int k = 0; k < 4; ++k) G.solid[k] = geo->side[k] == MLBM_SIDE_SOLID;
     G.n_disks = geo->n_disks;
-    G.L = L;
-    G.ell = std::fmin(8.0 * L, 0.5 * std::fmin(lx, ly));
+    G.L = (float)L;
+    G.ell = (float)std::fmin(8.0 * L, 0.5 * std::fmin(lx, ly));
     const double cj[dev::kRadii] = {1.0, 2.0, 4.0, 8.0};
-    for (int j = 0; j < dev::kRadii; ++j) G.rho[j] = std::fmin(cj[j] * L, 0.5 * std::fmin(lx, ly));
+    for (int j = 0; j < dev::kRadii; ++j) G.rho[j] = (float)std::fmin(cj[j] * L, 0.5 * std::fmin(lx, ly));
     double solid = 0.0;
     for (int k = 0; k < geo->n_disks; ++k) solid += dev::kPi * geo->disks[3 * k + 2] * geo->disks[3 * k + 2];
-    G.porosity = 1.0 - solid / (lx * ly);
+    G.porosity = (float)(1.0 - solid / (lx * ly));
     double* dxy = nullptr;
     double* ddisks = nullptr;
     cudaError_t e = cudaMalloc(&dxy, (size_t)n * 2 * sizeof(double));

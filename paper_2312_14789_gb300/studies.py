@@ -3,6 +3,7 @@
     python -m paper_2312_14789_gb300.studies batch [--samples 64] [--steps 20]
     python -m paper_2312_14789_gb300.studies warm [--train 512] [--test 64] [--nodes 200000]
     python -m paper_2312_14789_gb300.studies hybrid [--steps 200000] [--lattice-d 1.0]
+    python -m paper_2312_14789_gb300.studies porous [--nodes 1000000]
 
 batch: 64 porous samples (seeds 1000..1063) with node counts U(50k, 400k),
 porosity U(0.5, 0.85) and a mix of Darcy (s = 1) and inertial (s = 1/2, 1/4)
@@ -335,6 +336,59 @@ def hybrid_study(args):
     print(json.dumps(out))
 
 
+def porous_study(args):
+    """The ~1M-node porous box (porosity 0.7, radii U(8, 16), seed 3), tau = 1
+    (MLBM1), K = 16, interpolated bounce-back, from rest to steady state:
+    Darcy (s = 1, g = 1e-6) and faster flows at smaller streaming distances
+    (s = 1/2, 1/4, 1/8 with g chosen for a pore velocity of ~0.03, Re_d ~ 10-40).  Reports the
+    permeability, the pore Reynolds number Re_d = U_intrinsic d / nu (d the
+    mean disk diameter in lattice units d/s), steps and seconds to steady
+    state, the step throughput (autotuned, CUDA events) and its fraction of
+    the HBM roofline (481 algorithmic bytes per node-update)."""
+    import torch
+    from paper_2312_14789_gb300 import inputs as I
+    from paper_2312_14789_gb300 import mlbm
+    sys.path.insert(0, ROOT)
+    import bench
+
+    w = I.porous(seed=3, n_target=args.nodes, porosity=0.7)
+    d_mean = float(2 * w.disks[:, 2].mean())
+    peak = bench.peaks()[0]["hbm_gbs"]
+    out = {"study": "porous", "nodes": int(w.n), "porosity": w.meta["porosity"], "disks": int(len(w.disks)),
+           "runs": []}
+    for s_, g in ((1.0, 1e-6), (0.5, 8e-5), (0.25, 2e-5), (0.125, 5e-6)):
+        st = mlbm.build_stencils_for(w, K=16, s=s_, bb_mode=mlbm.BB_INTERPOLATED)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, g, 0.0))
+        variant, _ = mlbm.autotune(ctx, 10, flush_l2=True)
+        stream = torch.cuda.Stream()
+        mlbm.set_stream(ctx, stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            mlbm.step(ctx, 32)
+            e0.record(stream)
+            mlbm.step(ctx, 512)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / 512
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, g, 0.0))
+        mlbm.set_kernel_variant(ctx, variant)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps = mlbm.run_to_steady(ctx, 1e-7, 1000, 2_000_000, check=100)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        pm = mlbm.permeability(ctx)
+        nu = 0.5 / 3.0
+        out["runs"].append({"s": s_, "g": g, "variant": variant, "us_per_step": us, "mnups": w.n / us,
+                            "hbm_frac_of_measured_peak": w.n * 481 / (us * 1e-6) / 1e9 / peak,
+                            "steps_to_steady": int(steps), "seconds_to_steady": sec,
+                            "mnups_to_steady": w.n * steps / sec / 1e6,
+                            "k": pm["k"], "u_intrinsic": pm["u_intrinsic"], "tortuosity": pm["tortuosity"],
+                            "Re_d": pm["u_intrinsic"] * (d_mean / s_) / nu})
+        print(json.dumps(out["runs"][-1]), file=sys.stderr, flush=True)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -352,12 +406,16 @@ def main():
     w.add_argument("--seed", type=int, default=1)
     w.add_argument("--single", type=int, default=4)
     w.add_argument("--save", default="")
+    po = sub.add_parser("porous")
+    po.add_argument("--nodes", type=int, default=1_000_000)
     hb = sub.add_parser("hybrid")
     hb.add_argument("--steps", type=int, default=200_000)
     hb.add_argument("--lattice-d", type=float, default=1.0)
     args = ap.parse_args()
     if args.cmd == "hybrid":
         hybrid_study(args)
+    elif args.cmd == "porous":
+        porous_study(args)
     elif args.cmd == "batch":
         batch_study(args)
     elif args.cmd == "warm":

@@ -271,6 +271,31 @@ def test_porous_full_size_tau1_one_step_sampled():
     assert np.abs(b[t] - a).max() < 5 * pop_tol(1)
 
 
+@pytest.mark.parametrize("s,g", [(1.0, 1e-6), (0.25, 2e-5)])
+def test_porous_tau1_steady_state_matches_oracle(s, g):
+    """Body-force driven flow through a small porous box (~8k nodes, tau = 1,
+    interpolated bounce-back) from rest to steady state on the GPU (Darcy,
+    s = 1, and a faster flow at s = 1/4); the oracle runs the same number of
+    steps.  Laminar contract: relative L2 velocity error <= 1e-5, and the
+    permeability of the two fields within 1e-5."""
+    w = I.porous(seed=41, n_target=8000, porosity=0.7)
+    st = mlbm.build_stencils_for(w, K=16, s=s, bb_mode=1)
+    ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, g, 0.0))
+    steps = mlbm.run_to_steady(ctx, 1e-7, 1000, 60_000, check=100)
+    ru = mlbm.get_fields(ctx)
+    k = mlbm.permeability(ctx)["k"]
+    op = O.Operator(w, K=16, s=s, bb_mode=1).check()
+    ru0 = np.zeros((w.n, 3))
+    ru0[:, 0] = 1.0
+    ro = O.run_mlbm1(op, ru0, (g, 0.0), steps)
+    err = np.linalg.norm(ru[:, 1:] - ro[:, 1:]) / np.linalg.norm(ro[:, 1:])
+    assert err <= 1e-5, (steps, err)
+    box = (w.box[2] - w.box[0]) * (w.box[3] - w.box[1])
+    us, _ = O.mean_velocity(ro[:, 1], w.area, None, total_area=box)
+    ko = O.permeability(us, 1.0, g)
+    assert abs(k / ko - 1) <= 1e-5, (k, ko)
+
+
 # ------------------------------------------------------------ host features
 def test_save_load_continues_bitwise():
     w = I.poiseuille_channel(20, 16, 0.2, seed=3)
