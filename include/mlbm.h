@@ -379,6 +379,35 @@ int64_t mlbm_reduce_noalloc_max_nodes(void);
 mlbm_status mlbm_reduce_fields_device_noalloc(const float* rho, const float* ux, const float* uy, const float* area,
                                               const uint8_t* mask, int64_t n, double* out, void* stream);
 
+/* ------------------------------------------------ lattice LBM (comparison) */
+/*
+ * The paper's comparison method: lattice Boltzmann on a regular nx x ny grid
+ * (Sec. 2.1, Eq. (1)-(3): populations move one spacing per step), with the
+ * same FP32 collision as the meshless step (BGK, or TRT with tau_minus).
+ * cell[ny][nx] (row-major, host): 0 fluid, 1 solid (half-way bounce-back on
+ * the links that come from it), 2 equilibrium (the state is
+ * f^eq(rho_b, u_b) from eq_values[ny][nx][3] every step).  Links from
+ * outside a non-periodic side bounce back too.  Starts at rest (rho = 1,
+ * u = 0).  Populations in mlbm_lattice_set/get_populations are FP64
+ * [ny * nx][9] (unshifted).  mlbm_lattice_force is the momentum exchange on
+ * the bounce-back links, relative to the rest state (as mlbm_drag_lift):
+ * F = sum 2 (f*_k'(x) - w_k') e_k'.  mlbm_lattice_step is asynchronous on
+ * the lattice's own stream (mlbm_lattice_sync waits); the others are
+ * synchronous.  Sizes: 1 <= ny <= 65535, nx ny < 2^31.
+ * Errors: MLBM_E_INVALID, MLBM_E_CUDA, MLBM_E_OOM.
+ */
+typedef struct mlbm_lattice mlbm_lattice;
+mlbm_status mlbm_lattice_init(mlbm_lattice** out, int nx, int ny, int periodic_x, int periodic_y,
+                              const uint8_t* cell, const double* eq_values, const mlbm_params* p);
+void mlbm_lattice_destroy(mlbm_lattice* L);
+mlbm_status mlbm_lattice_step(mlbm_lattice* L, int64_t n_steps);
+mlbm_status mlbm_lattice_sync(mlbm_lattice* L);
+/* n_steps steps bracketed by CUDA events on the lattice's stream; *ms = their time */
+mlbm_status mlbm_lattice_time_steps(mlbm_lattice* L, int64_t n_steps, double* ms);
+mlbm_status mlbm_lattice_set_populations(mlbm_lattice* L, const double* f);
+mlbm_status mlbm_lattice_get_populations(mlbm_lattice* L, double* f);
+mlbm_status mlbm_lattice_force(mlbm_lattice* L, double* fx, double* fy);
+
 /* ------------------------------------------------------ learned warm start */
 /*
  * The paper starts every run from rest (Sec. 3.2: body-force driven flow

@@ -36,25 +36,32 @@ namespace dev {
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr float kPif = 3.14159265358979f;
 
-// area of the intersection of two circles of radii a and b, centres d apart
+// area of the intersection of two circles of radii a and b, centres d apart:
+// two circular segments cut by the common chord.  The chord's half-length
+// comes from the product form of Heron's formula and the segment angles from
+// atan2 of (half-chord, signed centre-to-chord distance), which stays well
+// conditioned in FP32 near tangency and near containment (acos of a cosine
+// near +-1 does not).
 __device__ float lens_area(float d, float a, float b) {
     if (d >= a + b) return 0.f;
     if (d <= fabsf(a - b)) {
         const float m = fminf(a, b);
         return kPif * m * m;
     }
-    const float ca = fminf(1.f, fmaxf(-1.f, (d * d + a * a - b * b) / (2.f * d * a)));
-    const float cb = fminf(1.f, fmaxf(-1.f, (d * d + b * b - a * a) / (2.f * d * b)));
     const float k = fmaxf(0.f, (-d + a + b) * (d + a - b) * (d - a + b) * (d + a + b));
-    return a * a * acosf(ca) + b * b * acosf(cb) - 0.5f * sqrtf(k);
+    const float hc = sqrtf(k) / (2.f * d);
+    const float xa = (d * d + a * a - b * b) / (2.f * d);  // signed distance from centre A to the chord
+    const float xb = d - xa;
+    return a * a * atan2f(hc, xa) - xa * hc + b * b * atan2f(hc, xb) - xb * hc;
 }
 
 // area of the part of a circle of radius a beyond a line at signed distance h
-// from its centre
+// from its centre (half-angle from atan2 for the same reason)
 __device__ float segment_area(float h, float a) {
     if (h >= a) return 0.f;
     if (h <= -a) return kPif * a * a;
-    return a * a * acosf(h / a) - h * sqrtf((a - h) * (a + h));
+    const float hc = sqrtf((a - h) * (a + h));
+    return a * a * atan2f(hc, h) - h * hc;
 }
 
 constexpr int kRadii = 4;

@@ -116,6 +116,14 @@ def lib():
                                                _vp, _vp]),
                 "mlbm_features_device": (st, [_vp, _vp, _dbl, _vp]),
                 "mlbm_warm_start": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
+                "mlbm_lattice_init": (st, [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp]),
+                "mlbm_lattice_destroy": (None, [_vp]),
+                "mlbm_lattice_step": (st, [_vp, _i64]),
+                "mlbm_lattice_sync": (st, [_vp]),
+                "mlbm_lattice_time_steps": (st, [_vp, _i64, _vp]),
+                "mlbm_lattice_set_populations": (st, [_vp, _vp]),
+                "mlbm_lattice_get_populations": (st, [_vp, _vp]),
+                "mlbm_lattice_force": (st, [_vp, _vp, _vp]),
                 "mlbm_last_error": (ctypes.c_char_p, []),
                 "mlbm_version": (ctypes.c_char_p, []),
             }
@@ -498,3 +506,49 @@ def warm_start(ctx: Context, mlp: Mlp, X_ptr, scale_u, scale_rho=None) -> int:
     cold = ctypes.c_int()
     _check(lib().mlbm_warm_start(ctx.handle, mlp.handle, _vp(X_ptr), _ptr(su), _ptr(sr), ctypes.byref(cold)))
     return cold.value
+
+
+# ------------------------------------------------------ lattice LBM (comparison)
+class Lattice:
+    """Regular-grid LBM of the library (the paper's comparison method)."""
+
+    def __init__(self, cell, params: Params, periodic=(True, True), eq_values=None):
+        cell = np.ascontiguousarray(cell, dtype=np.uint8)
+        self.ny, self.nx = cell.shape
+        eqv = None if eq_values is None else _f64(np.asarray(eq_values).reshape(-1, 3))
+        p = _Params(int(params.model), float(params.tau), float(params.tau_minus), float(params.gx), float(params.gy))
+        h = _vp()
+        _check(lib().mlbm_lattice_init(ctypes.byref(h), self.nx, self.ny, int(bool(periodic[0])),
+                                       int(bool(periodic[1])), _ptr(cell), _ptr(eqv), ctypes.byref(p)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.mlbm_lattice_destroy(self.handle)
+            self.handle = None
+
+    def step(self, n: int = 1):
+        _check(lib().mlbm_lattice_step(self.handle, int(n)))
+
+    def sync(self):
+        _check(lib().mlbm_lattice_sync(self.handle))
+
+    def time_steps(self, n: int) -> float:
+        """Milliseconds for n steps (CUDA events on the lattice's stream)."""
+        ms = ctypes.c_double()
+        _check(lib().mlbm_lattice_time_steps(self.handle, int(n), ctypes.byref(ms)))
+        return ms.value
+
+    def set_populations(self, f):
+        a = _f64(np.asarray(f).reshape(-1, 9))
+        _check(lib().mlbm_lattice_set_populations(self.handle, _ptr(a)))
+
+    def get_populations(self) -> np.ndarray:
+        a = np.empty((self.nx * self.ny, 9))
+        _check(lib().mlbm_lattice_get_populations(self.handle, _ptr(a)))
+        return a
+
+    def force(self) -> tuple:
+        fx, fy = ctypes.c_double(), ctypes.c_double()
+        _check(lib().mlbm_lattice_force(self.handle, ctypes.byref(fx), ctypes.byref(fy)))
+        return fx.value, fy.value

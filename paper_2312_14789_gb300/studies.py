@@ -4,6 +4,7 @@
     python -m paper_2312_14789_gb300.studies warm [--train 512] [--test 64] [--nodes 200000]
     python -m paper_2312_14789_gb300.studies hybrid [--steps 200000] [--lattice-d 1.0]
     python -m paper_2312_14789_gb300.studies porous [--nodes 1000000]
+    python -m paper_2312_14789_gb300.studies lbm [--steps 200000]
 
 batch: 64 porous samples (seeds 1000..1063) with node counts U(50k, 400k),
 porosity U(0.5, 0.85) and a mix of Darcy (s = 1) and inertial (s = 1/2, 1/4)
@@ -389,6 +390,99 @@ def porous_study(args):
     print(json.dumps(out))
 
 
+def lattice_karman(d_lb, u0=0.05, length_d=22.0, height_d=4.1, center_d=(2.0, 2.0)):
+    """Cells of the vortex-street channel on a regular lattice: D = d_lb
+    spacings, equilibrium cells on the four sides (parabolic inflow and
+    outflow with maximum u0, rest on the top and bottom), solid cells whose
+    centre lies inside the cylinder."""
+    nx, ny = int(round(length_d * d_lb)), int(round(height_d * d_lb))
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    cx, cy, r = center_d[0] * d_lb, center_d[1] * d_lb, 0.5 * d_lb
+    cell = np.zeros((ny, nx), np.uint8)
+    cell[(x - cx) ** 2 + (y - cy) ** 2 < r * r] = 1
+    side = (x == 0) | (x == nx - 1) | (y == 0) | (y == ny - 1)
+    cell[side] = 2
+    eqv = np.zeros((ny, nx, 3))
+    eqv[..., 0] = 1.0
+    h = ny - 1.0
+    lr = (x == 0) | (x == nx - 1)
+    eqv[..., 1] = np.where(lr & ~((y == 0) | (y == ny - 1)), 4.0 * u0 * y * (h - y) / (h * h), 0.0)
+    return cell, eqv
+
+
+def lbm_study(args):
+    """The paper's comparison, lattice LBM vs meshless LBM (Sec. 3.1), on
+    GB300: the vortex street at Re = 100 on the regular lattice with D = 80
+    spacings (the lattice resolution of the meshless run with D = 40 node
+    spacings and s = 1/2, so both take the same time step) against the
+    meshless step on the scattered and the hybrid node sets.  Per method:
+    nodes, time per step (CUDA events, back to back), algorithmic bytes per
+    step, Strouhal number and mean drag over the second half of --steps."""
+    import torch
+    from paper_2312_14789_gb300 import inputs as I
+    from paper_2312_14789_gb300 import mlbm
+
+    re_, u0, d = 100, 0.05, 40.0
+    s_ = 0.5
+    d_lb = d / s_
+    tau = 3.0 * u0 * d_lb / re_ + 0.5
+    every = 50
+    out = {"study": "lbm", "Re": re_, "D_lattice_units": d_lb, "tau": tau, "steps": args.steps}
+
+    def timed(step_fn, stream, n=2048):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            step_fn(32)
+            e0.record(stream)
+            step_fn(n)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / n
+
+    # lattice LBM
+    cell, eqv = lattice_karman(d_lb, u0)
+    lat = mlbm.Lattice(cell, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0), periodic=(False, False), eq_values=eqv)
+    lat.time_steps(32)
+    us_lat = lat.time_steps(2048) * 1e3 / 2048
+    lat = mlbm.Lattice(cell, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0), periodic=(False, False), eq_values=eqv)
+    cd, cl = np.empty(args.steps // every), np.empty(args.steps // every)
+    for i in range(len(cd)):
+        lat.step(every)
+        fx, fy = lat.force()
+        cd[i], cl[i] = 2 * fx / (u0 ** 2 * d_lb), 2 * fy / (u0 ** 2 * d_lb)
+    h = len(cd) // 2
+    n_lat = int((cell != 1).sum())
+    out["lattice"] = {"cells": int(cell.size), "fluid_and_boundary_cells": n_lat, "us_per_step": us_lat,
+                      "mnups": n_lat / us_lat, "algorithmic_bytes_per_step": int(cell.size) * 73,
+                      "strouhal": _strouhal(cl[h:], every, d_lb, u0), "cd_mean": float(np.mean(cd[h:])),
+                      "cl_amplitude": float(np.ptp(cl[h:]) / 2)}
+    print(json.dumps(out["lattice"]), file=sys.stderr, flush=True)
+    # meshless on the scattered and the hybrid node sets
+    for name, w in (("meshless_scattered", I.karman(seed=2)),
+                    ("meshless_hybrid", I.karman(seed=2, lattice_beyond_d=1.0))):
+        st = mlbm.build_stencils_for(w, K=16, s=s_, bb_mode=mlbm.BB_SIMPLE)
+        info = mlbm.stencils_info(st)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
+        variant, _ = mlbm.autotune(ctx, 10)
+        stream = torch.cuda.Stream()
+        mlbm.set_stream(ctx, stream.cuda_stream)
+        us = timed(lambda k: mlbm.step(ctx, k), stream)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
+        mlbm.set_kernel_variant(ctx, variant)
+        for i in range(len(cd)):
+            mlbm.step(ctx, every)
+            _, _, cd[i], cl[i] = mlbm.drag_lift(ctx, d, u0)
+        import bench
+        out[name] = {"nodes": int(w.n), "n_lagrange": info["n_lagrange"], "variant": variant, "us_per_step": us,
+                     "mnups": w.n / us, "algorithmic_bytes_per_step": int(bench.algorithmic_bytes(info, 16)),
+                     "strouhal": _strouhal(cl[h:], every, d_lb, u0), "cd_mean": float(np.mean(cd[h:])),
+                     "cl_amplitude": float(np.ptp(cl[h:]) / 2)}
+        print(json.dumps(out[name]), file=sys.stderr, flush=True)
+    for name in ("meshless_scattered", "meshless_hybrid"):
+        out[name]["time_per_step_over_lattice"] = out[name]["us_per_step"] / out["lattice"]["us_per_step"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -408,12 +502,16 @@ def main():
     w.add_argument("--save", default="")
     po = sub.add_parser("porous")
     po.add_argument("--nodes", type=int, default=1_000_000)
+    lb = sub.add_parser("lbm")
+    lb.add_argument("--steps", type=int, default=200_000)
     hb = sub.add_parser("hybrid")
     hb.add_argument("--steps", type=int, default=200_000)
     hb.add_argument("--lattice-d", type=float, default=1.0)
     args = ap.parse_args()
     if args.cmd == "hybrid":
         hybrid_study(args)
+    elif args.cmd == "lbm":
+        lbm_study(args)
     elif args.cmd == "porous":
         porous_study(args)
     elif args.cmd == "batch":
