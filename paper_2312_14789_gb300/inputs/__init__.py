@@ -104,6 +104,53 @@ def _sample(box, periodic, rgrid, disks, clear_frac, fixed, seed, max_out, k_tri
     return out[:n].copy()
 
 
+def fluid_voronoi_areas(xy, box, periodic, disks, spacing, fine=None):
+    """Area of the part of each node's Voronoi cell that lies in the fluid:
+    the box minus the solid disks is rastered on a regular grid (spacing
+    `spacing`; `fine` = (x0, y0, x1, y1, spacing) rasters that window more
+    finely), every fluid raster point goes to its nearest node (minimum image
+    across periodic sides) and carries its raster cell's area."""
+    from scipy.spatial import cKDTree
+    x0, y0, x1, y1 = box
+    lx, ly = x1 - x0, y1 - y0
+    pts = np.asarray(xy, np.float64)
+    shift = np.array([x0, y0])
+    boxsize = None
+    if periodic[0] or periodic[1]:
+        boxsize = np.array([lx if periodic[0] else 1e30, ly if periodic[1] else 1e30])
+        pts = np.mod(pts - shift, [lx if periodic[0] else 1e30, ly if periodic[1] else 1e30])
+    else:
+        pts = pts - shift
+    tree = cKDTree(pts, boxsize=boxsize)
+    area = np.zeros(len(pts))
+    windows = []
+    if fine is not None:
+        windows.append(fine)
+    windows.append((x0, y0, x1, y1, spacing))
+    for wi, (wx0, wy0, wx1, wy1, d) in enumerate(windows):
+        nx_, ny_ = max(1, int(np.ceil((wx1 - wx0) / d))), max(1, int(np.ceil((wy1 - wy0) / d)))
+        dx, dy = (wx1 - wx0) / nx_, (wy1 - wy0) / ny_
+        xs = wx0 + (np.arange(nx_) + 0.5) * dx
+        for row in range(0, ny_, 256):
+            ys = wy0 + (np.arange(row, min(ny_, row + 256)) + 0.5) * dy
+            X, Y = np.meshgrid(xs, ys)
+            m = np.ones(X.shape, bool)
+            for cx, cy, r in np.asarray(disks).reshape(-1, 3):
+                ddx = X - cx
+                if periodic[0]:
+                    ddx -= lx * np.rint(ddx / lx)
+                m &= ddx * ddx + (Y - cy) ** 2 >= r * r
+            if wi > 0 and fine is not None:
+                fx0, fy0, fx1, fy1, _ = fine
+                m &= ~((X >= fx0) & (X < fx1) & (Y >= fy0) & (Y < fy1))
+            q = np.stack([X[m] - x0, Y[m] - y0], 1)
+            if boxsize is not None:
+                q = np.mod(q, [lx if periodic[0] else 1e30, ly if periodic[1] else 1e30])
+            _, j = tree.query(q, workers=-1)
+            area += np.bincount(j, minlength=len(pts)) * (dx * dy)
+    return area
+
+
 # --------------------------------------------------------------------------
 # Plain grids
 # --------------------------------------------------------------------------
@@ -189,7 +236,7 @@ def poiseuille_channel(nx: int = 40, ny: int = 50, jitter: float = 0.2, seed: in
 def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: float = 4.1,
            center_d: tuple = (2.0, 2.0), U0: float = 0.05, r_fine: float = 0.37, r_coarse: float = 0.74,
            fine_band_d: float = 1.5, blend_to_d: float = 4.0, scale: float = 1.0,
-           lattice_beyond_d: float | None = None) -> Workload:
+           lattice_beyond_d: float | None = None, areas: str = "spacing") -> Workload:
     """Channel length_d*D x height_d*D with a solid cylinder of diameter D.
 
     Lengths are in units of the reference spacing h_ref=1, so D is the number
@@ -269,9 +316,16 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     fx = np.clip(pts[:, 0] / lx * (nrx - 1), 0, nrx - 1.000001)
     fy = np.clip(pts[:, 1] / ly * (nry - 1), 0, nry - 1.000001)
     r_at = rgrid[fy.astype(int), fx.astype(int)]
-    area = r_at ** 2
-    area *= (lx * ly - np.pi * R * R) / area.sum()
-    name = f"karman_D{D:g}_s{seed}" + ("" if lattice_beyond_d is None else f"_hybrid{lattice_beyond_d:g}")
+    if areas == "voronoi":
+        reach = R + (fine_band_d + 0.5) * D
+        fine = (max(0.0, cx - reach), max(0.0, cy - reach), min(lx, cx + reach), min(ly, cy + reach), 0.05 * D / 40.0)
+        area = fluid_voronoi_areas(pts, (0.0, 0.0, lx, ly), (False, False), np.array([[cx, cy, R]]),
+                                   0.25 * D / 40.0, fine)
+    else:
+        area = r_at ** 2
+        area *= (lx * ly - np.pi * R * R) / area.sum()
+    name = f"karman_D{D:g}_s{seed}" + ("" if lattice_beyond_d is None else f"_hybrid{lattice_beyond_d:g}") + \
+        ("" if areas == "spacing" else "_" + areas)
     return Workload(name, pts, cls, (0.0, 0.0, lx, ly), (OPEN,) * 4,
                     np.array([[cx, cy, R]]), eqv, area, 1.0,
                     {"D": D, "U0": U0, "H": ly, "L": lx, "seed": seed, "n_eq": nf, "n_wall": m,
@@ -309,12 +363,15 @@ def _rsa_disks(rng, lx, ly, porosity, rmin, rmax, gap, wall_gap, max_tries=40000
 
 def porous(seed: int = 3, n_target: int = 1_000_000, porosity: float = 0.7, rmin: float = 8.0,
            rmax: float = 16.0, h: float = 1.0, gap: float = 2.0, r_pd: float = 0.84,
-           side: float | None = None) -> Workload:
+           side: float | None = None, areas: str = "uniform") -> Workload:
     """Square box of random non-overlapping solid disks (radii U(rmin, rmax) in
     units of h), periodic in x, solid walls at y=0 and y=L.  Wall nodes sit on
     every solid surface (arc spacing about h); fluid nodes are Poisson-disk
     samples of radius r_pd*h that keep r_pd*h from the wall nodes.  The side
-    length is chosen so the fluid holds about n_target nodes."""
+    length is chosen so the fluid holds about n_target nodes.  areas:
+    "uniform" (fluid area / n for every node) or "voronoi" (the fluid part of
+    each node's Voronoi cell, rastered at 0.2h; wall nodes own about half a
+    cell)."""
     rng = np.random.default_rng(seed)
     density = 0.68 / (r_pd * h) ** 2          # nodes per unit area for Bridson sampling
     if side is None:
@@ -343,9 +400,13 @@ def porous(seed: int = 3, n_target: int = 1_000_000, porosity: float = 0.7, rmin
     cls = np.zeros(n, np.uint8)
     cls[:len(fixed)] = WALL
     fluid_area = lx * ly - np.sum(np.pi * disks[:, 2] ** 2)
-    area = np.full(n, fluid_area / n)
+    if areas == "voronoi":
+        area = fluid_voronoi_areas(pts, (0.0, 0.0, lx, ly), (True, False), disks, 0.2 * h)
+    else:
+        area = np.full(n, fluid_area / n)
     phi = fluid_area / (lx * ly)
-    return Workload(f"porous_n{n}_s{seed}", pts, cls, (0.0, 0.0, lx, ly), (PERIODIC, PERIODIC, SOLID, SOLID),
+    return Workload(f"porous_n{n}_s{seed}" + ("" if areas == "uniform" else "_" + areas), pts, cls,
+                    (0.0, 0.0, lx, ly), (PERIODIC, PERIODIC, SOLID, SOLID),
                     disks, np.zeros((n, 3)), area, h,
                     {"seed": seed, "porosity": float(phi), "n_disks": len(disks), "L": lx,
                      "mean_d": float(2 * disks[:, 2].mean()) if len(disks) else 0.0})

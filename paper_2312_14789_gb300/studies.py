@@ -352,10 +352,11 @@ def porous_study(args):
     sys.path.insert(0, ROOT)
     import bench
 
-    w = I.porous(seed=3, n_target=args.nodes, porosity=0.7)
+    w = I.porous(seed=3, n_target=args.nodes, porosity=0.7, areas=args.areas)
     d_mean = float(2 * w.disks[:, 2].mean())
     peak = bench.peaks()[0]["hbm_gbs"]
     out = {"study": "porous", "nodes": int(w.n), "porosity": w.meta["porosity"], "disks": int(len(w.disks)),
+           "node_areas": args.areas,
            "runs": []}
     for s_, g in ((1.0, 1e-6), (0.5, 8e-5), (0.25, 2e-5), (0.125, 5e-6)):
         st = mlbm.build_stencils_for(w, K=16, s=s_, bb_mode=mlbm.BB_INTERPOLATED)
@@ -427,7 +428,8 @@ def lbm_study(args):
     d_lb = d / s_
     tau = 3.0 * u0 * d_lb / re_ + 0.5
     every = 50
-    out = {"study": "lbm", "Re": re_, "D_lattice_units": d_lb, "tau": tau, "steps": args.steps}
+    out = {"study": "lbm", "Re": re_, "D_lattice_units": d_lb, "tau": tau, "steps": args.steps,
+           "node_areas": args.areas}
 
     def timed(step_fn, stream, n=2048):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -458,8 +460,8 @@ def lbm_study(args):
                       "cl_amplitude": float(np.ptp(cl[h:]) / 2)}
     print(json.dumps(out["lattice"]), file=sys.stderr, flush=True)
     # meshless on the scattered and the hybrid node sets
-    for name, w in (("meshless_scattered", I.karman(seed=2)),
-                    ("meshless_hybrid", I.karman(seed=2, lattice_beyond_d=1.0))):
+    for name, w in (("meshless_scattered", I.karman(seed=2, areas=args.areas)),
+                    ("meshless_hybrid", I.karman(seed=2, lattice_beyond_d=1.0, areas=args.areas))):
         st = mlbm.build_stencils_for(w, K=16, s=s_, bb_mode=mlbm.BB_SIMPLE)
         info = mlbm.stencils_info(st)
         ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
@@ -502,8 +504,10 @@ def main():
     w.add_argument("--save", default="")
     po = sub.add_parser("porous")
     po.add_argument("--nodes", type=int, default=1_000_000)
+    po.add_argument("--areas", default="voronoi", choices=["uniform", "voronoi"])
     lb = sub.add_parser("lbm")
     lb.add_argument("--steps", type=int, default=200_000)
+    lb.add_argument("--areas", default="voronoi", choices=["spacing", "voronoi"])
     hb = sub.add_parser("hybrid")
     hb.add_argument("--steps", type=int, default=200_000)
     hb.add_argument("--lattice-d", type=float, default=1.0)
