@@ -236,7 +236,7 @@ def poiseuille_channel(nx: int = 40, ny: int = 50, jitter: float = 0.2, seed: in
 def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: float = 4.1,
            center_d: tuple = (2.0, 2.0), U0: float = 0.05, r_fine: float = 0.37, r_coarse: float = 0.74,
            fine_band_d: float = 1.5, blend_to_d: float = 4.0, scale: float = 1.0,
-           lattice_beyond_d: float | None = None, areas: str = "spacing") -> Workload:
+           lattice_beyond_d: float | None = None, areas: str = "voronoi") -> Workload:
     """Channel length_d*D x height_d*D with a solid cylinder of diameter D.
 
     Lengths are in units of the reference spacing h_ref=1, so D is the number
@@ -318,9 +318,8 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     r_at = rgrid[fy.astype(int), fx.astype(int)]
     if areas == "voronoi":
         reach = R + (fine_band_d + 0.5) * D
-        fine = (max(0.0, cx - reach), max(0.0, cy - reach), min(lx, cx + reach), min(ly, cy + reach), 0.05 * D / 40.0)
-        area = fluid_voronoi_areas(pts, (0.0, 0.0, lx, ly), (False, False), np.array([[cx, cy, R]]),
-                                   0.25 * D / 40.0, fine)
+        fine = (max(0.0, cx - reach), max(0.0, cy - reach), min(lx, cx + reach), min(ly, cy + reach), 0.05)
+        area = fluid_voronoi_areas(pts, (0.0, 0.0, lx, ly), (False, False), np.array([[cx, cy, R]]), 0.25, fine)
     else:
         area = r_at ** 2
         area *= (lx * ly - np.pi * R * R) / area.sum()
