@@ -275,8 +275,12 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        for 4 blocks, one group at a time; 16 = as 15, persistent with L2
  *        prefetch; 17 = capped for 4 blocks, two groups at a time (BGK only;
  *        the tau = 1 model runs variant 11 for these numbers)
+ *   18-19 as 10 without the bounce-back code (fewer registers), registers
+ *        capped for 2 / 3 resident blocks of 256, followed by a second kernel
+ *        that recomputes every node with bounce-back links in full and
+ *        overwrites its output (BGK only; tau = 1 runs variant 11)
  * Variants 4 and up are available for K = 12, 16, 24 and 32.
- * The default is 4 when available, else 1.  mlbm_autotune times every
+ * The default is 12 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream
  * (state saved and restored, step count unchanged), keeps the fastest and
  * returns its per-step time in *best_ms (may be NULL).

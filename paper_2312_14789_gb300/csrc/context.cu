@@ -81,6 +81,7 @@ struct mlbm_ctx {
 
 namespace {
 constexpr int kGraphSteps = 16;
+constexpr int kMaxVariant = 19;  // step kernel variants 0..19 (see mlbm_set_kernel_variant)
 }
 
 namespace {
@@ -306,6 +307,8 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     c->S.link_slot = c->link_slot;
     c->S.links = c->links;
     c->S.eqv = c->eqv;
+    c->S.link_nodes = c->link_nodes;
+    c->S.n_link_nodes = c->n_link_nodes;
     set_collide(c);
     // ---- initial state
     std::vector<double> ru((size_t)n * 3);
@@ -677,7 +680,7 @@ mlbm_status mlbm_load(mlbm_ctx* c, const char* path) {
 
 mlbm_status mlbm_set_kernel_variant(mlbm_ctx* c, int variant) {
     if (!c) return set_error(MLBM_E_INVALID, "set_kernel_variant: NULL context");
-    if (variant < 0 || variant > 17 || (variant >= 4 && !tma_supported(c->K / 4)))
+    if (variant < 0 || variant > kMaxVariant || (variant >= 4 && !tma_supported(c->K / 4)))
         return set_error(MLBM_E_INVALID, "set_kernel_variant: variant not available for this K");
     c->variant = variant;
     return MLBM_OK;
@@ -728,7 +731,7 @@ mlbm_status mlbm_autotune_ex(mlbm_ctx* c, int steps_per_variant, int flush_l2, d
     }
     int best = c->variant;
     double best_t = 1e30;
-    for (int v = 0; v <= 17 && st == MLBM_OK; ++v) {
+    for (int v = 0; v <= kMaxVariant && st == MLBM_OK; ++v) {
         if (v >= 14 && c->params.model != MLBM_MODEL_BGK) continue;
         if (v >= 4 && !tma_supported(c->K / 4)) continue;
         // one untimed warm-up launch, then the timed ones

@@ -49,6 +49,9 @@ struct Stencil {
     // parameters of each sample (both null for a single sample)
     const uint16_t* node_sample;
     const Collide* coll;
+    // positions of the nodes with bounce-back links (for the split variants)
+    const int* link_nodes;
+    int n_link_nodes;
 };
 
 // collision parameters of node p

@@ -29,7 +29,9 @@ namespace dev {
 // ------------------------------------------------------------ BGK / TRT
 // LPN lanes (1 or 2) cooperate on one node: lane h takes the neighbour groups
 // q = h, h + LPN, ... and the partial sums are combined with a pair shuffle.
-template <int KQ, int LPN>
+// LINKS = false leaves out the bounce-back overrides (the split variants
+// recompute the nodes with links in a second pass)
+template <int KQ, int LPN, bool LINKS = true>
 __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restrict__ f8in,
                                          const float* __restrict__ f0in, float4* __restrict__ f8out,
                                          float* __restrict__ f0out, const Collide& C0, int p, int h, unsigned grp) {
@@ -101,7 +103,7 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
         float own[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] += own[k];
-        if (meta & 4) {
+        if (LINKS && (meta & 4)) {
             // bounce-back links (rare): every lane of the node computes them
             const LinkRec L = S.links[S.link_slot[p]];
 #pragma unroll
@@ -339,6 +341,35 @@ __global__ void __launch_bounds__(256, MINB) bgk_step_persistent(Stencil S, cons
         const int p = tile * TN + threadIdx.x / LPN;
         if (p < S.n) bgk_node<KQ, LPN>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
     }
+}
+
+// Split form: the persistent pass without the bounce-back code (fewer
+// registers, more resident warps), then one thread per node with links
+// recomputes that node completely and overwrites its output.
+template <int KQ, int MINB>
+__global__ void __launch_bounds__(256, MINB) bgk_step_nolink(Stencil S, const float4* __restrict__ f8in,
+                                                             const float* __restrict__ f0in,
+                                                             float4* __restrict__ f8out, float* __restrict__ f0out,
+                                                             Collide C, int dist) {
+    constexpr int TN = 256;
+    const int n_tiles = (S.n + TN - 1) / TN;
+    const unsigned lane = threadIdx.x & 31u;
+    if (threadIdx.x < 32)
+        for (int d = 0; d < dist; ++d) prefetch_tile<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (threadIdx.x < 32) prefetch_tile<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
+        const int p = tile * TN + threadIdx.x;
+        if (p < S.n) bgk_node<KQ, 1, false>(S, f8in, f0in, f8out, f0out, C, p, 0, 1u << lane);
+    }
+}
+
+template <int KQ>
+__global__ void __launch_bounds__(128) bgk_link_nodes(Stencil S, const float4* __restrict__ f8in,
+                                                      const float* __restrict__ f0in, float4* __restrict__ f8out,
+                                                      float* __restrict__ f0out, Collide C) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S.n_link_nodes) return;
+    bgk_node<KQ, 1, true>(S, f8in, f0in, f8out, f0out, C, S.link_nodes[e], 0, 1u << (threadIdx.x & 31u));
 }
 
 // --------------------------------------------------------- tau = 1 (MLBM1)
@@ -908,6 +939,19 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
         case 15: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_split_kernel<KQC, 4, 1><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         case 16: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_split_persistent<KQC, 4, 1>, 128, S.n, st, [&](int g) { dev::bgk_split_persistent<KQC, 4, 1><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
         case 17: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_split_kernel<KQC, 4, 2><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 18:
+        case 19: {
+            // the second pass reads f8in only and writes the link nodes' outputs after the first pass
+            if (variant == 18) {
+                MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_nolink<KQC, 2>, 256, S.n, st, [&](int g) { dev::bgk_step_nolink<KQC, 2><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); })));
+            } else {
+                MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_nolink<KQC, 3>, 256, S.n, st, [&](int g) { dev::bgk_step_nolink<KQC, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); })));
+            }
+            if (S.n_link_nodes > 0) {
+                MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_link_nodes<KQC><<<(S.n_link_nodes + 127) / 128, 128, 0, st>>>(S, f8in, f0in, f8out, f0out, C)));
+            }
+            break;
+        }
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -931,7 +975,9 @@ cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* ou
         case 14:
         case 15:
         case 16:
-        case 17:  // the direction split exists for the populations of the BGK state only
+        case 17:
+        case 18:
+        case 19:  // the direction split and the link split exist for the BGK state only
             MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
         default: return cudaErrorInvalidValue;
     }

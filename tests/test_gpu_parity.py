@@ -48,7 +48,7 @@ def gpu_ctx(w, K, s, bb_mode, params, sigma=0.7071067811865476, use_lagrange=Tru
     return ctx
 
 
-VARIANTS = list(range(18))
+VARIANTS = list(range(20))
 
 
 # ----------------------------------------------------------------- plain MLBM
@@ -355,7 +355,7 @@ def test_autotune_keeps_state_and_picks_a_variant():
     mlbm.step(ctx, 5)
     before = mlbm.get_fields(ctx)
     v, ms = mlbm.autotune(ctx, 5)
-    assert 0 <= v <= 17 and ms > 0
+    assert 0 <= v <= 19 and ms > 0
     assert mlbm.step_count(ctx) == 5
     assert np.array_equal(mlbm.get_fields(ctx), before)
 
