@@ -74,8 +74,10 @@ def lib():
             L.oracle_bc_links.restype = i32
             L.oracle_bc_links.argtypes = [dbl, dbl, dbl, vp, vp, vp, i32, vp, vp]
             L.oracle_assemble.restype = None
-            L.oracle_assemble.argtypes = [i64, vp, i32, vp, vp, vp, vp, dbl, dbl, i32, i32, dbl, vp, vp,
+            L.oracle_assemble.argtypes = [i64, vp, i32, vp, vp, vp, vp, dbl, dbl, i32, i32, i32, dbl, vp, vp,
                                           vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.oracle_rbf_weights.restype = i32
+            L.oracle_rbf_weights.argtypes = [vp, i32, dbl, dbl, vp]
             L.oracle_mlbm_step.restype = None
             L.oracle_mlbm_step.argtypes = [i64, vp, i64, vp, i32, vp, vp, vp, vp, vp, dbl, dbl, dbl, dbl, vp]
             L.oracle_mlbm1_step.restype = None
@@ -176,6 +178,18 @@ def wls_matrix(off, s, sigma_factor):
     return st, M
 
 
+def rbf_weights(off, d):
+    """RBF-FD weights (cubic polyharmonic spline with quadratic augmentation)
+    of the stencil offsets off[K][2] for the value at the point d = (dx, dy)."""
+    off = _c(off, np.float64)
+    K = off.shape[0]
+    w = np.empty(K)
+    st = lib().oracle_rbf_weights(_p(off), K, float(d[0]), float(d[1]), _p(w))
+    if st:
+        raise ValueError(f"RBF-FD system singular (status {st})")
+    return w
+
+
 def lagrange_detect(off, s=1.0, link=None, q=None, bb_mode=1, tol=1e-9):
     """Returns (found, slot[9], h, centre direction m) for one stencil."""
     off = _c(off, np.float64)
@@ -216,7 +230,7 @@ class Operator:
     workload, either for all nodes or for a subset `targets`."""
 
     def __init__(self, w, K, s, sigma_factor=0.7071067811865476, bb_mode=1, use_lagrange=True,
-                 lag_tol=1e-9, targets=None):
+                 lag_tol=1e-9, targets=None, interp="wls"):
         self.w = w
         self.K, self.s, self.bb_mode = int(K), float(s), int(bb_mode)
         self.sigma_factor = float(sigma_factor)
@@ -242,6 +256,7 @@ class Operator:
         xy = _c(w.xy, np.float64)
         lib().oracle_assemble(nt, _p(self.targets), K, _p(self.idx), _p(self.off), _p(xy), _p(cls),
                               self.s, self.sigma_factor, self.bb_mode, int(bool(use_lagrange)),
+                              {"wls": 0, "rbf": 1}[interp],
                               float(lag_tol), _p(box), _p(side), _p(disks) if len(disks) else None,
                               len(disks), _p(self.kind), _p(self.M), _p(self.lag_slot), _p(self.lag_h),
                               _p(self.lag_center), _p(self.link), _p(self.q), _p(self.W), _p(self.src),

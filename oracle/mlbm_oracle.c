@@ -427,6 +427,69 @@ int oracle_bc_links(double x, double y, double s, const double* box, const int* 
  * self_slot: stencil position of the node itself.
  * w_out: [9][K] (row 0 unused, zero).
  */
+/*
+ * RBF-FD weights (Sec. 2.2: the paper's interpolant, polyharmonic spline
+ * phi(r) = r^3 augmented with the quadratic monomials): for the stencil
+ * offsets o_j (j < K) and an evaluation point d, the weights w solve
+ *     [ Phi  P ] [ w      ]   [ phi(|o_i - d|) ]
+ *     [ P^T  0 ] [ lambda ] = [ p(d)           ]
+ * with Phi_ij = |o_i - o_j|^3 and P_ia = p_a(o_i), p = (1, x, y, x^2, xy, y^2);
+ * then sum_j w_j f_j is the value at d of the cubic-PHS interpolant of the
+ * data f_j with quadratic augmentation.  Coordinates are divided by the
+ * largest offset first (the weights do not change: r^3 is homogeneous and
+ * the quadratic space is closed under scaling).  Gauss-Jordan elimination
+ * with partial pivoting in long double; returns 2 on a singular system.
+ */
+int oracle_rbf_weights(const double* off, int K, double dx, double dy, double* w_out) {
+    const int N = K + 6;
+    if (K > 64) return 1;
+    double rK = 0;
+    for (int j = 0; j < K; ++j) {
+        double r = sqrt(off[2 * j] * off[2 * j] + off[2 * j + 1] * off[2 * j + 1]);
+        if (r > rK) rK = r;
+    }
+    if (!(rK > 0)) return 2;
+    long double A[70][71];
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j <= N; ++j) A[i][j] = 0;
+    for (int i = 0; i < K; ++i) {
+        const double xi = off[2 * i] / rK, yi = off[2 * i + 1] / rK;
+        for (int j = 0; j < K; ++j) {
+            const double ex = xi - off[2 * j] / rK, ey = yi - off[2 * j + 1] / rK;
+            const double r = sqrt(ex * ex + ey * ey);
+            A[i][j] = (long double)r * r * r;
+        }
+        double p[6];
+        obasis(xi, yi, p);
+        for (int a = 0; a < 6; ++a) {
+            A[i][K + a] = p[a];
+            A[K + a][i] = p[a];
+        }
+        const double qx = xi - dx / rK, qy = yi - dy / rK;
+        const double rq = sqrt(qx * qx + qy * qy);
+        A[i][N] = (long double)rq * rq * rq;
+    }
+    double pd[6];
+    obasis(dx / rK, dy / rK, pd);
+    for (int a = 0; a < 6; ++a) A[K + a][N] = pd[a];
+    for (int c = 0; c < N; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < N; ++r)
+            if (fabsl(A[r][c]) > fabsl(A[piv][c])) piv = r;
+        if (fabsl(A[piv][c]) < 1e-300L) return 2;
+        if (piv != c)
+            for (int b = 0; b <= N; ++b) { long double t = A[c][b]; A[c][b] = A[piv][b]; A[piv][b] = t; }
+        for (int r = 0; r < N; ++r) {
+            if (r == c) continue;
+            long double m = A[r][c] / A[c][c];
+            if (m == 0.0L) continue;
+            for (int b = c; b <= N; ++b) A[r][b] -= m * A[c][b];
+        }
+    }
+    for (int j = 0; j < K; ++j) w_out[j] = (double)(A[j][N] / A[j][j]);
+    return 0;
+}
+
 void oracle_direction_weights(int K, int kind, const double* M, const int* lag_slot, double lag_h,
                               int lag_center, double s, int self_slot, const int* link, const double* q,
                               int bb_mode, double* w_out, int* src_out) {
@@ -605,7 +668,8 @@ void oracle_force_mlbm1(int64_t nt, const int64_t* targets, int K, const int64_t
 /*
  * Everything the step needs for each target node, from its stencil
  * (idx/off from oracle_knn): the WLS matrix or the Lagrange block, the
- * bounce-back links and the per-direction weights.
+ * bounce-back links and the per-direction weights (interp = 1: the
+ * least-squares rows are replaced by RBF-FD rows at the same points).
  *   kind[t]: 0 WLS, 1 Lagrange (only when use_lagrange), 2 equilibrium node
  *            (no weights needed)
  *   status[t]: 0, or the code of the failing routine (2 degenerate stencil,
@@ -615,7 +679,7 @@ void oracle_force_mlbm1(int64_t nt, const int64_t* targets, int K, const int64_t
  */
 void oracle_assemble(int64_t nt, const int64_t* targets, int K, const int64_t* idx, const double* off,
                      const double* xy, const uint8_t* node_class, double s, double sigma_factor,
-                     int bb_mode, int use_lagrange, double lag_tol, const double* box, const int* side,
+                     int bb_mode, int use_lagrange, int interp, double lag_tol, const double* box, const int* side,
                      const double* disks, int ndisks, int* kind, double* M, int* lag_slot,
                      double* lag_h, int* lag_center, int* link, double* q, double* W, int* src,
                      int* status) {
@@ -648,5 +712,13 @@ void oracle_assemble(int64_t nt, const int64_t* targets, int K, const int64_t* i
         }
         oracle_direction_weights(K, kind[t], M + 6 * K * t, lag_slot + 9 * t, lag_h[t], lag_center[t], s,
                                  self_slot, link + 9 * t, q + 9 * t, bb_mode, W + 9 * K * t, src + 9 * t);
+        if (interp == 1 && kind[t] == 0) {
+            /* RBF-FD rows replace the least-squares rows at the same points */
+            for (int k = 1; k < 9; ++k) {
+                if (!use[k]) continue;
+                st = oracle_rbf_weights(o, K, dx[k], dy[k], W + (9 * t + k) * K);
+                if (st) { status[t] = st; break; }
+            }
+        }
     }
 }
