@@ -59,6 +59,9 @@ enum { MLBM_SIDE_PERIODIC = 0, MLBM_SIDE_SOLID = 1, MLBM_SIDE_OPEN = 2 };
 enum { MLBM_BB_SIMPLE = 0, MLBM_BB_INTERPOLATED = 1 };
 /* collision model */
 enum { MLBM_MODEL_BGK = 0, MLBM_MODEL_TAU1 = 1 };
+/* interpolant of the scattered (non-Lagrange) nodes: quadratic weighted least
+   squares, or RBF-FD (cubic polyharmonic spline with quadratic terms, Sec. 2.2) */
+enum { MLBM_INTERP_WLS = 0, MLBM_INTERP_RBF = 1 };
 /* device node order: Hilbert curve (default), Morton (Z) curve, strips of
    about 8 node spacings left to right, or the caller's order */
 enum { MLBM_ORDER_HILBERT = 0, MLBM_ORDER_MORTON = 1, MLBM_ORDER_ROWS = 2, MLBM_ORDER_INPUT = 3 };
@@ -116,6 +119,25 @@ typedef struct {
 mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
                                 double sigma_factor, int bb_mode, int use_lagrange, mlbm_stencils** out);
 
+/*
+ * mlbm_build_stencils with a choice of interpolant for the scattered nodes.
+ * MLBM_INTERP_RBF is the paper's RBF-FD (Sec. 2.2): the cubic polyharmonic
+ * spline r^3 augmented with the six quadratic monomials, over the node's own
+ * K-node stencil (the paper notes that for small streaming distances the
+ * Eulerian node's stencil decides the interpolation).  For every direction
+ * the weights of the value at its departure point (or at the reflected point
+ * of an interpolated bounce-back link) solve the (K+6)-square saddle-point
+ * system in FP64 (LU, partial pivoting); they are stored per direction, 8 K
+ * FP32 weights per node.  Lagrange blocks and simple bounce-back are as for
+ * the least-squares fit.  RBF-FD stencils serve BGK contexts (mlbm_init
+ * returns MLBM_E_INVALID for the tau = 1 model with them).  Errors: as
+ * mlbm_build_stencils; a singular RBF-FD system gives
+ * MLBM_E_SINGULAR_STENCIL.
+ */
+mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
+                                   double sigma_factor, int bb_mode, int use_lagrange, int interp,
+                                   mlbm_stencils** out);
+
 void mlbm_stencils_free(mlbm_stencils* st);
 
 typedef struct {
@@ -155,6 +177,10 @@ int mlbm_stencils_order(const mlbm_stencils* st);
  */
 mlbm_status mlbm_stencils_export(const mlbm_stencils* st, int64_t* idx, double* M, int32_t* kind,
                                  int32_t* link_mask, double* q, double* lag_h, int32_t* lag_center);
+/* RBF-FD stencils: W[n][9][K] (caller's order; columns in the stencil's
+   search order, as idx of mlbm_stencils_export; row 0 and the rows of
+   directions that do not interpolate are zero).  Errors: MLBM_E_INVALID. */
+mlbm_status mlbm_stencils_export_weights(const mlbm_stencils* st, double* W);
 
 /* ----------------------------------------------------------------- context */
 typedef struct {

@@ -30,6 +30,8 @@ struct HostStencils {
     std::vector<int64_t> inv;      // caller id -> position
     std::vector<int32_t> idx;      // [n][K] neighbour positions, search order
     std::vector<double> M;         // [n][6][K] least-squares matrix, units of s
+    int interp = 0;                // MLBM_INTERP_*
+    std::vector<double> Wr;        // [n][8][K] RBF-FD weights of directions 1..8 (RBF stencils)
     std::vector<uint8_t> kind;     // Kind
     std::vector<uint8_t> center;   // Lagrange block centre direction m
     std::vector<double> lag_h;     // Lagrange block spacing

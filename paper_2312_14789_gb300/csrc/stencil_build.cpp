@@ -218,6 +218,68 @@ int wls_qr(const double* off, int K, double s, double sigma_factor, double* M) {
     return 0;
 }
 
+// RBF-FD weights of the stencil for the value at (dx, dy) (Sec. 2.2): the
+// cubic polyharmonic spline with quadratic augmentation.  The saddle-point
+// system [Phi P; P^T 0] [w; l] = [phi(|o_i - d|); p(d)] is solved by LU with
+// partial pivoting in FP64, coordinates scaled by the largest offset (the
+// weights are scale-free).  Returns 0, or 2 for a numerically singular
+// system (smallest pivot below 1e-13 of the largest).
+int rbf_weights(const double* off, int K, double dx, double dy, double* w) {
+    const int N = K + 6;
+    double rK = 0;
+    for (int j = 0; j < K; ++j) rK = std::max(rK, std::hypot(off[2 * j], off[2 * j + 1]));
+    if (!(rK > 0)) return 2;
+    double A[38][38], b[38], u[32], v[32];
+    for (int j = 0; j < K; ++j) {
+        u[j] = off[2 * j] / rK;
+        v[j] = off[2 * j + 1] / rK;
+    }
+    const double du = dx / rK, dv = dy / rK;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) A[i][j] = 0.0;
+    for (int i = 0; i < K; ++i) {
+        for (int j = 0; j < K; ++j) {
+            const double r = std::hypot(u[i] - u[j], v[i] - v[j]);
+            A[i][j] = r * r * r;
+        }
+        const double p[6] = {1.0, u[i], v[i], u[i] * u[i], u[i] * v[i], v[i] * v[i]};
+        for (int a = 0; a < 6; ++a) A[i][K + a] = A[K + a][i] = p[a];
+        const double r = std::hypot(u[i] - du, v[i] - dv);
+        b[i] = r * r * r;
+    }
+    const double pd[6] = {1.0, du, dv, du * du, du * dv, dv * dv};
+    for (int a = 0; a < 6; ++a) b[K + a] = pd[a];
+    double pmax = 0, pmin = 1e300;
+    for (int c = 0; c < N; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < N; ++r)
+            if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        if (piv != c) {
+            for (int j = 0; j < N; ++j) std::swap(A[c][j], A[piv][j]);
+            std::swap(b[c], b[piv]);
+        }
+        const double d = A[c][c];
+        pmax = std::max(pmax, std::fabs(d));
+        pmin = std::min(pmin, std::fabs(d));
+        if (d == 0.0) return 2;
+        for (int r = c + 1; r < N; ++r) {
+            const double m = A[r][c] / d;
+            if (m == 0.0) continue;
+            for (int j = c; j < N; ++j) A[r][j] -= m * A[c][j];
+            b[r] -= m * b[c];
+        }
+    }
+    if (pmin < 1e-13 * pmax) return 2;
+    double x[38];
+    for (int r = N - 1; r >= 0; --r) {
+        double acc = b[r];
+        for (int j = r + 1; j < N; ++j) acc -= A[r][j] * x[j];
+        x[r] = acc / A[r][r];
+    }
+    for (int j = 0; j < K; ++j) w[j] = x[j];
+    return 0;
+}
+
 // Departure offsets and which directions interpolate (simple bounce-back
 // links copy the node's own population instead).
 void departures(double s, uint16_t mask, const double* q, int bb_mode, double* dx, double* dy, bool* use) {
@@ -400,7 +462,15 @@ using namespace mlbm;
 extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
                                            double sigma_factor, int bb_mode, int use_lagrange,
                                            mlbm_stencils** out) {
+    return mlbm_build_stencils_ex(nodes, geo, K, s, sigma_factor, bb_mode, use_lagrange, MLBM_INTERP_WLS, out);
+}
+
+extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
+                                              double sigma_factor, int bb_mode, int use_lagrange, int interp,
+                                              mlbm_stencils** out) {
     clear_error();
+    if (interp != MLBM_INTERP_WLS && interp != MLBM_INTERP_RBF)
+        return set_error(MLBM_E_INVALID, "build_stencils: bad interpolant");
     if (!out) return set_error(MLBM_E_INVALID, "build_stencils: out is NULL");
     *out = nullptr;
     if (!nodes || !geo || !nodes->xy || !nodes->node_class)
@@ -443,6 +513,7 @@ extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_g
     H.K = K;
     H.s = s;
     H.bb_mode = bb_mode;
+    H.interp = interp;
     H.box_area = b.lx * b.ly;
     const double* xy = nodes->xy;
     const CellGrid grid = make_grid(xy, n, b, K);
@@ -451,6 +522,7 @@ extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_g
     std::vector<int64_t> nid((size_t)n * K);
     std::vector<double> off((size_t)n * K * 2);
     std::vector<double> Mc((size_t)n * 6 * K, 0.0);
+    std::vector<double> Wc(interp == MLBM_INTERP_RBF ? (size_t)n * 8 * K : 0, 0.0);
     std::vector<uint8_t> kind(n), center(n, 0);
     std::vector<double> lagh(n, 0.0), qc((size_t)n * 9, 0.0);
     std::vector<int8_t> slot((size_t)n * 9, 0);
@@ -483,6 +555,10 @@ extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_g
             }
             kind[i] = kKindWls;
             code = wls_qr(&off[(size_t)i * K * 2], K, s, sigma_factor, &Mc[(size_t)i * 6 * K]);
+            if (!code && interp == MLBM_INTERP_RBF)
+                for (int k = 1; k < 9 && !code; ++k)
+                    if (use[k])
+                        code = rbf_weights(&off[(size_t)i * K * 2], K, dx[k], dy[k], &Wc[((size_t)i * 8 + k - 1) * K]);
             if (code) {
 #pragma omp critical
                 { if (bad_node < 0 || i < bad_node) { bad_node = i; bad_code = code; } }
@@ -510,6 +586,7 @@ extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_g
 
     H.idx.resize((size_t)n * K);
     H.M.assign((size_t)n * 6 * K, 0.0);
+    H.Wr.assign(interp == MLBM_INTERP_RBF ? (size_t)n * 8 * K : 0, 0.0);
     H.kind.resize(n);
     H.center.resize(n);
     H.lag_h.resize(n);
@@ -527,6 +604,7 @@ extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_g
         const int64_t i = H.perm[p];
         for (int j = 0; j < K; ++j) H.idx[(size_t)p * K + j] = (int32_t)H.inv[nid[(size_t)i * K + j]];
         std::memcpy(&H.M[(size_t)p * 6 * K], &Mc[(size_t)i * 6 * K], sizeof(double) * 6 * K);
+        if (!Wc.empty()) std::memcpy(&H.Wr[(size_t)p * 8 * K], &Wc[(size_t)i * 8 * K], sizeof(double) * 8 * K);
         H.kind[p] = kind[i];
         H.center[p] = center[i];
         H.lag_h[p] = lagh[i];
@@ -606,6 +684,7 @@ extern "C" mlbm_status mlbm_stencils_set_order(mlbm_stencils* st, int order) {
         }
     }
     move(H.M, (size_t)6 * K);
+    if (!H.Wr.empty()) move(H.Wr, (size_t)8 * K);
     move(H.kind, 1);
     move(H.center, 1);
     move(H.lag_h, 1);
@@ -622,3 +701,16 @@ extern "C" mlbm_status mlbm_stencils_set_order(mlbm_stencils* st, int order) {
 }
 
 extern "C" int mlbm_stencils_order(const mlbm_stencils* st) { return st ? st->h.order : -1; }
+
+extern "C" mlbm_status mlbm_stencils_export_weights(const mlbm_stencils* st, double* W) {
+    if (!st || !W) return set_error(MLBM_E_INVALID, "stencils_export_weights: NULL argument");
+    const HostStencils& H = st->h;
+    if (H.interp != MLBM_INTERP_RBF) return set_error(MLBM_E_INVALID, "stencils_export_weights: not RBF-FD stencils");
+    const int K = H.K;
+    for (int64_t p = 0; p < H.n; ++p) {
+        const int64_t i = H.perm[p];
+        std::memset(&W[(size_t)i * 9 * K], 0, sizeof(double) * K);
+        std::memcpy(&W[((size_t)i * 9 + 1) * K], &H.Wr[(size_t)p * 8 * K], sizeof(double) * 8 * K);
+    }
+    return MLBM_OK;
+}

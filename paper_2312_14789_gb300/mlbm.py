@@ -16,6 +16,7 @@ import numpy as np
 from . import _build
 
 MODEL_BGK, MODEL_TAU1 = 0, 1
+INTERP_WLS, INTERP_RBF = 0, 1
 ORDER_HILBERT, ORDER_MORTON, ORDER_ROWS, ORDER_INPUT = 0, 1, 2, 3
 BB_SIMPLE, BB_INTERPOLATED = 0, 1
 NODE_FLUID, NODE_WALL, NODE_EQ = 0, 1, 2
@@ -64,6 +65,8 @@ def lib():
             st = ctypes.c_int
             sig = {
                 "mlbm_build_stencils": (st, [_vp, _vp, _i32, _dbl, _dbl, _i32, _i32, _vp]),
+                "mlbm_build_stencils_ex": (st, [_vp, _vp, _i32, _dbl, _dbl, _i32, _i32, _i32, _vp]),
+                "mlbm_stencils_export_weights": (st, [_vp, _vp]),
                 "mlbm_stencils_free": (None, [_vp]),
                 "mlbm_stencils_info": (st, [_vp, _vp]),
                 "mlbm_stencils_set_order": (st, [_vp, _i32]),
@@ -165,7 +168,8 @@ class Stencils:
 
 
 def build_stencils(xy, node_class, box, sides, disks=None, eq_values=None, area=None, K=16, s=1.0,
-                   sigma_factor=0.7071067811865476, bb_mode=BB_INTERPOLATED, use_lagrange=True) -> Stencils:
+                   sigma_factor=0.7071067811865476, bb_mode=BB_INTERPOLATED, use_lagrange=True,
+                   interp=INTERP_WLS) -> Stencils:
     xy = _f64(xy)
     n = xy.shape[0]
     cls = np.ascontiguousarray(node_class, dtype=np.uint8)
@@ -176,8 +180,9 @@ def build_stencils(xy, node_class, box, sides, disks=None, eq_values=None, area=
     geo = _Geometry(float(box[0]), float(box[1]), float(box[2]), float(box[3]), (_i32 * 4)(*[int(v) for v in sides]),
                     len(dk), _ptr(dk) if len(dk) else None)
     h = _vp()
-    _check(lib().mlbm_build_stencils(ctypes.byref(nodes), ctypes.byref(geo), int(K), float(s), float(sigma_factor),
-                                     int(bb_mode), int(bool(use_lagrange)), ctypes.byref(h)))
+    _check(lib().mlbm_build_stencils_ex(ctypes.byref(nodes), ctypes.byref(geo), int(K), float(s),
+                                        float(sigma_factor), int(bb_mode), int(bool(use_lagrange)), int(interp),
+                                        ctypes.byref(h)))
     return Stencils(h, n, int(K), None)
 
 
@@ -190,6 +195,13 @@ def stencils_info(st: Stencils) -> dict:
     info = _Info()
     _check(lib().mlbm_stencils_info(st.handle, ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in _Info._fields_}
+
+
+def stencils_export_weights(st: Stencils) -> np.ndarray:
+    """RBF-FD stencils: per-direction weights [n][9][K] in the caller's order."""
+    W = np.empty((st.n, 9, st.K))
+    _check(lib().mlbm_stencils_export_weights(st.handle, _ptr(W)))
+    return W
 
 
 def stencils_set_order(st: Stencils, order: int):

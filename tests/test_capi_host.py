@@ -121,3 +121,25 @@ def test_reordering_keeps_the_stencils(order):
         assert np.array_equal(ref[k], got[k]), k
     with pytest.raises(mlbm.MlbmError):
         mlbm.stencils_set_order(st, 7)
+
+
+@pytest.mark.parametrize("case", ["porous", "karman"])
+def test_builder_rbf_weights_match_oracle(case):
+    """RBF-FD weights of the host builder (FP64 LU) against the oracle's
+    (long-double Gauss-Jordan) for every interpolated direction, including
+    the reflected points of interpolated bounce-back links."""
+    if case == "porous":
+        w, s, bb = I.porous(seed=5, n_target=4000), 0.5, 1
+    else:
+        w, s, bb = I.karman(seed=2, scale=0.25), 0.5, 0
+    st = mlbm.build_stencils_for(w, K=16, s=s, bb_mode=bb, interp=mlbm.INTERP_RBF)
+    W = mlbm.stencils_export_weights(st)
+    ex = mlbm.stencils_export(st)
+    op = O.Operator(w, K=16, s=s, bb_mode=bb, interp="rbf").check()
+    assert np.array_equal(ex["kind"], op.kind)
+    assert np.array_equal(ex["idx"], op.idx)
+    sel = op.kind == 0
+    for k in range(1, 9):
+        interp_k = sel & ~((op.link[:, k] != 0) & (bb == 0))
+        err = np.abs(W[interp_k, k] - op.W[interp_k, k]).max()
+        assert err < 1e-8, (k, err)
