@@ -156,7 +156,7 @@ mlbm_status sync(mlbm_ctx* c) {
 mlbm_status launch_one_step(mlbm_ctx* c, int variant) {
     const int a = c->cur, b = c->cur ^ 1;
     const int model = c->params.model == MLBM_MODEL_BGK ? 0 : 1;
-    if (variant >= 4 && variant <= 7)
+    if (variant >= 4 && variant <= 7 && !c->S.Wr)
         MLBM_CUDA(launch_step_tma(variant, model, c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->ruv[a], c->ruv[b],
                                   c->C, c->err, c->stream));
     else if (model == 0)
@@ -181,8 +181,12 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     const int64_t n = H.n, np = c->n_pad;
     const int K = H.K, Kq = K / 4;
     // ---- host-side device layout
+    if (H.interp == MLBM_INTERP_RBF && p->model != MLBM_MODEL_BGK)
+        return set_error(MLBM_E_INVALID, "init: RBF-FD stencils serve the BGK model only");
+    const bool rbf = H.interp == MLBM_INTERP_RBF;
     std::vector<int32_t> hidx((size_t)Kq * np * 4, 0);
     std::vector<float> hM((size_t)6 * Kq * np * 4, 0.f);
+    std::vector<float> hW(rbf ? (size_t)8 * Kq * np * 4 : 0, 0.f);
     std::vector<uint8_t> hmeta(np, 0), hmask(np, 0);
     std::vector<float> hlag(np, 0.f), harea(np, 0.f), has2(np, 0.f);
     std::vector<int> hslot(np, -1), hperm(np, 0), hlinknodes;
@@ -215,6 +219,10 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
                                      m[1], m[2]};
                 for (int a = 0; a < 6; ++a)
                     hM[(((size_t)(a * Kq + jj / 4)) * np + q) * 4 + (jj % 4)] = (float)t[a];
+                if (rbf)
+                    for (int k = 0; k < 8; ++k)
+                        hW[(((size_t)(k * Kq + jj / 4)) * np + q) * 4 + (jj % 4)] =
+                            (float)H.Wr[((size_t)q * 8 + k) * K + j];
             }
         } else if (kind == kKindLagrange) {
             for (int b = 0; b < 9; ++b) {
@@ -238,6 +246,8 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     // ---- device buffers
     MLBM_TRY(dalloc(c, &c->idx, (size_t)Kq * np));
     MLBM_TRY(dalloc(c, &c->M, (size_t)6 * Kq * np));
+    float4* dW = nullptr;
+    if (rbf) MLBM_TRY(dalloc(c, &dW, (size_t)8 * Kq * np));
     MLBM_TRY(dalloc(c, &c->meta, np));
     MLBM_TRY(dalloc(c, &c->mask, np));
     MLBM_TRY(dalloc(c, &c->lag_r, np));
@@ -276,6 +286,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     if (!tma_supported(Kq)) c->variant = 1;  // variants >= 4 exist for K in {12, 16, 24, 32}
     MLBM_TRY(upload(c, c->idx, hidx.data(), hidx.size() * 4));
     MLBM_TRY(upload(c, c->M, hM.data(), hM.size() * 4));
+    if (rbf) MLBM_TRY(upload(c, dW, hW.data(), hW.size() * 4));
     MLBM_TRY(upload(c, c->meta, hmeta.data(), np));
     MLBM_TRY(upload(c, c->mask, hmask.data(), np));
     MLBM_TRY(upload(c, c->lag_r, hlag.data(), np * 4));
@@ -308,6 +319,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     c->S.links = c->links;
     c->S.eqv = c->eqv;
     c->S.link_nodes = c->link_nodes;
+    c->S.Wr = dW;
     c->S.n_link_nodes = c->n_link_nodes;
     set_collide(c);
     // ---- initial state
@@ -809,8 +821,9 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
         if (!sts[i]) return set_error(MLBM_E_INVALID, "batch_init: NULL stencils");
         MLBM_TRY(check_params(&params[i]));
         if (sts[i]->h.K != sts[0]->h.K || sts[i]->h.bb_mode != sts[0]->h.bb_mode ||
-            params[i].model != params[0].model)
-            return set_error(MLBM_E_INVALID, "batch_init: samples must share K, bounce-back rule and model");
+            params[i].model != params[0].model || sts[i]->h.interp != sts[0]->h.interp)
+            return set_error(MLBM_E_INVALID,
+                             "batch_init: samples must share K, bounce-back rule, interpolant and model");
     }
     // concatenate the samples' host stencils; sample i keeps its own Hilbert
     // order inside positions [off_i, off_i + n_i)
@@ -821,6 +834,7 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
     C.K = K;
     C.s = sts[0]->h.s;
     C.bb_mode = sts[0]->h.bb_mode;
+    C.interp = sts[0]->h.interp;
     std::vector<int64_t> off(n_samples + 1, 0);
     for (int i = 0; i < n_samples; ++i) off[i + 1] = off[i] + sts[i]->h.n;
     const int64_t n = off[n_samples];
@@ -846,6 +860,10 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
             node_sample[o + p] = (uint16_t)i;
         }
         std::copy(H.M.begin(), H.M.end(), C.M.begin() + (size_t)o * 6 * K);
+        if (C.interp == MLBM_INTERP_RBF) {
+            if (C.Wr.empty()) C.Wr.assign((size_t)n * 8 * K, 0.0);
+            std::copy(H.Wr.begin(), H.Wr.end(), C.Wr.begin() + (size_t)o * 8 * K);
+        }
         std::copy(H.kind.begin(), H.kind.end(), C.kind.begin() + o);
         std::copy(H.center.begin(), H.center.end(), C.center.begin() + o);
         std::copy(H.lag_h.begin(), H.lag_h.end(), C.lag_h.begin() + o);

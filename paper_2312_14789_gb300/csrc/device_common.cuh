@@ -52,6 +52,9 @@ struct Stencil {
     // positions of the nodes with bounce-back links (for the split variants)
     const int* link_nodes;
     int n_link_nodes;
+    // RBF-FD stencils: per-direction weights [8 K/4][n_pad] float4 (row
+    // r = direction k - 1), null for the least-squares fit
+    const float4* Wr;
 };
 
 // collision parameters of node p
@@ -145,6 +148,26 @@ __device__ __forceinline__ void wls_acc(const float4* __restrict__ f8, int j, fl
     acc[5] = fmaf(Hh, a6, fmaf(Wp, a6, acc[5]));
     acc[6] = fmaf(G, a7, fmaf(W, a7, acc[6]));
     acc[7] = fmaf(-Hh, a8, fmaf(Wp, a8, acc[7]));
+}
+
+// RBF-FD value of population k_src of the stencil at the point whose
+// weights are row r of node p (centred on the node's own value, the weights
+// sum to one)
+template <int KQ>
+__device__ __forceinline__ float rbf_general(const Stencil& S, const float4* __restrict__ f8, int p, int r,
+                                             int k_src) {
+    const float own = pop(f8, p, k_src);
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        const int4 id = __ldg(S.idx + (size_t)q * S.n_pad + p);
+        const float4 w = __ldg(S.Wr + (size_t)(r * KQ + q) * S.n_pad + p);
+        acc = fmaf(w.x, pop(f8, id.x, k_src) - own, acc);
+        acc = fmaf(w.y, pop(f8, id.y, k_src) - own, acc);
+        acc = fmaf(w.z, pop(f8, id.z, k_src) - own, acc);
+        acc = fmaf(w.w, pop(f8, id.w, k_src) - own, acc);
+    }
+    return own + acc;
 }
 
 template <int KQ>

@@ -30,8 +30,9 @@ namespace dev {
 // LPN lanes (1 or 2) cooperate on one node: lane h takes the neighbour groups
 // q = h, h + LPN, ... and the partial sums are combined with a pair shuffle.
 // LINKS = false leaves out the bounce-back overrides (the split variants
-// recompute the nodes with links in a second pass)
-template <int KQ, int LPN, bool LINKS = true>
+// recompute the nodes with links in a second pass); RBF = true interpolates
+// the least-squares-kind nodes with their stored RBF-FD weights
+template <int KQ, int LPN, bool LINKS = true, bool RBF = false>
 __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restrict__ f8in,
                                          const float* __restrict__ f0in, float4* __restrict__ f8out,
                                          float* __restrict__ f0out, const Collide& C0, int p, int h, unsigned grp) {
@@ -51,7 +52,36 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
         const float cy = (kind == 1) ? (float)ey_of(meta >> 4) : 0.f;
         const float4 oa = __ldg(f8in + 2 * (size_t)p);
         const float4 ob = __ldg(f8in + 2 * (size_t)p + 1);
-        if (kind == 0) {
+        if (kind == 0 && RBF) {
+            // f_k(x) = own_k + sum_j w_kj (f_k(j) - own_k), weights per direction
+#pragma unroll
+            for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
+                const int q = i * LPN + h;
+                if (q < KQ) {
+                    const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                    float wt[8][4];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float4 w4 = ld_stream(S.Wr + (size_t)(k * KQ + q) * S.n_pad + p);
+                        wt[k][0] = w4.x; wt[k][1] = w4.y; wt[k][2] = w4.z; wt[k][3] = w4.w;
+                    }
+                    const int ids[4] = {id.x, id.y, id.z, id.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float4 ra = __ldg(f8in + 2 * (size_t)ids[c]);
+                        const float4 rb = __ldg(f8in + 2 * (size_t)ids[c] + 1);
+                        acc[0] = fmaf(wt[0][c], ra.x - oa.x, acc[0]);
+                        acc[1] = fmaf(wt[1][c], ra.y - oa.y, acc[1]);
+                        acc[2] = fmaf(wt[2][c], ra.z - oa.z, acc[2]);
+                        acc[3] = fmaf(wt[3][c], ra.w - oa.w, acc[3]);
+                        acc[4] = fmaf(wt[4][c], rb.x - ob.x, acc[4]);
+                        acc[5] = fmaf(wt[5][c], rb.y - ob.y, acc[5]);
+                        acc[6] = fmaf(wt[6][c], rb.z - ob.z, acc[6]);
+                        acc[7] = fmaf(wt[7][c], rb.w - ob.w, acc[7]);
+                    }
+                }
+            }
+        } else if (kind == 0) {
 #pragma unroll
             for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
                 const int q = i * LPN + h;
@@ -112,6 +142,8 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
                 const int kp = opp_of(k);
                 if (S.bb_mode == 0) {
                     acc[k - 1] = own[kp - 1];
+                } else if (kind == 0 && RBF) {
+                    acc[k - 1] = rbf_general<KQ>(S, f8in, p, k - 1, kp);
                 } else if (kind == 0) {
                     float pb[6];
                     basis_at(k, L.t[k - 1], pb);
@@ -370,6 +402,49 @@ __global__ void __launch_bounds__(128) bgk_link_nodes(Stencil S, const float4* _
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= S.n_link_nodes) return;
     bgk_node<KQ, 1, true>(S, f8in, f0in, f8out, f0out, C, S.link_nodes[e], 0, 1u << (threadIdx.x & 31u));
+}
+
+// RBF-FD stencils: one lane per node, the per-direction weights streamed
+// instead of the least-squares matrix; plain grid or persistent blocks that
+// prefetch later tiles' weight, index and meta rows into L2.
+template <int KQ>
+__device__ __forceinline__ void prefetch_tile_rbf(const Stencil& S, int base, int tn, unsigned lane) {
+    if (base >= S.n) return;
+    const int nodes = min(tn, S.n_pad - base);
+    for (int c = (int)lane; c < 9 * KQ + 1; c += 32) {
+        if (c < 8 * KQ)
+            prefetch_l2(S.Wr + (size_t)c * S.n_pad + base, (uint32_t)nodes * 16u);
+        else if (c < 9 * KQ)
+            prefetch_l2(S.idx + (size_t)(c - 8 * KQ) * S.n_pad + base, (uint32_t)nodes * 16u);
+        else
+            prefetch_l2(S.meta + base, (uint32_t)((nodes + 15) / 16 * 16));
+    }
+}
+
+template <int KQ, int MINB>
+__global__ void __launch_bounds__(256, MINB) bgk_step_rbf(Stencil S, const float4* __restrict__ f8in,
+                                                          const float* __restrict__ f0in, float4* __restrict__ f8out,
+                                                          float* __restrict__ f0out, Collide C) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.n) return;
+    bgk_node<KQ, 1, true, true>(S, f8in, f0in, f8out, f0out, C, p, 0, 1u << (threadIdx.x & 31u));
+}
+
+template <int KQ, int MINB>
+__global__ void __launch_bounds__(256, MINB) bgk_step_rbf_persistent(Stencil S, const float4* __restrict__ f8in,
+                                                                     const float* __restrict__ f0in,
+                                                                     float4* __restrict__ f8out,
+                                                                     float* __restrict__ f0out, Collide C, int dist) {
+    constexpr int TN = 256;
+    const int n_tiles = (S.n + TN - 1) / TN;
+    const unsigned lane = threadIdx.x & 31u;
+    if (threadIdx.x < 32)
+        for (int d = 0; d < dist; ++d) prefetch_tile_rbf<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (threadIdx.x < 32) prefetch_tile_rbf<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
+        const int p = tile * TN + threadIdx.x;
+        if (p < S.n) bgk_node<KQ, 1, true, true>(S, f8in, f0in, f8out, f0out, C, p, 0, 1u << lane);
+    }
 }
 
 // --------------------------------------------------------- tau = 1 (MLBM1)
@@ -695,6 +770,8 @@ __global__ void __launch_bounds__(128) force_kernel(Stencil S, int model, int n_
             if (model == 0) {
                 if (S.bb_mode == 0) {
                     val = pop(st8, p, kp);
+                } else if (kind == 0 && S.Wr) {
+                    val = rbf_general<KQ>(S, st8, p, k - 1, kp);
                 } else if (kind == 0) {
                     float pb[6];
                     basis_at(k, L.t[k - 1], pb);
@@ -924,6 +1001,21 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
                             float* f0out, const dev::Collide& C, int variant, cudaStream_t st) {
     if (S.n == 0) return cudaSuccess;
     const int block = 256;
+    if (S.Wr) {
+        // RBF-FD stencils: variants 10 and 12 map to the persistent kernel
+        // (uncapped / 2 blocks per SM), 0 to the plain uncapped kernel, the
+        // rest to the plain kernel capped for 2 blocks per SM
+        if (variant == 10) {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_rbf_persistent<KQC, 1>, 256, S.n, st, [&](int g) { dev::bgk_step_rbf_persistent<KQC, 1><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); })));
+        } else if (variant == 12) {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_rbf_persistent<KQC, 2>, 256, S.n, st, [&](int g) { dev::bgk_step_rbf_persistent<KQC, 2><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); })));
+        } else if (variant == 0) {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_rbf<KQC, 1><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C)));
+        } else {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_rbf<KQC, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C)));
+        }
+        return cudaGetLastError();
+    }
     switch (variant) {
         case 0: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 1, 1><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         case 1: MLBM_DISPATCH_KQ(S.Kq, (dev::bgk_step_kernel<KQC, 2, 1><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;

@@ -5,6 +5,7 @@
     python -m paper_2312_14789_gb300.studies hybrid [--steps 200000] [--lattice-d 1.0]
     python -m paper_2312_14789_gb300.studies porous [--nodes 1000000]
     python -m paper_2312_14789_gb300.studies lbm [--steps 200000]
+    python -m paper_2312_14789_gb300.studies rbf [--steps 200000]
 
 batch: 64 porous samples (seeds 1000..1063) with node counts U(50k, 400k),
 porosity U(0.5, 0.85) and a mix of Darcy (s = 1) and inertial (s = 1/2, 1/4)
@@ -485,6 +486,48 @@ def lbm_study(args):
     print(json.dumps(out))
 
 
+def rbf_study(args):
+    """The paper's RBF-FD interpolant against the least-squares fit on the
+    vortex street (Re = 100, s = 1/2, scattered node set, fluid-Voronoi
+    areas): step time with the L2 flushed before every step (autotuned), its
+    fraction of the HBM roofline (algorithmic bytes: 4 (9 + 9) + 32 K + 4 K + 1
+    per RBF-FD node, 4 (9 + 9) + 24 K + 4 K + 1 per least-squares node), and
+    the Strouhal number and mean drag after --steps steps from rest."""
+    from paper_2312_14789_gb300 import inputs as I
+    from paper_2312_14789_gb300 import mlbm
+    sys.path.insert(0, ROOT)
+    import bench
+
+    re_, s_, u0, d = 100, 0.5, 0.05, 40.0
+    tau = 3.0 * u0 * (d / s_) / re_ + 0.5
+    peak = bench.peaks()[0]["hbm_gbs"]
+    w = I.karman(seed=2)
+    every = 50
+    out = {"study": "rbf", "Re": re_, "s": s_, "tau": tau, "steps": args.steps, "nodes": int(w.n)}
+    for name, interp, K in (("wls_K16", mlbm.INTERP_WLS, 16), ("rbf_K16", mlbm.INTERP_RBF, 16),
+                            ("rbf_K24", mlbm.INTERP_RBF, 24)):
+        st = mlbm.build_stencils_for(w, K=K, s=s_, bb_mode=mlbm.BB_SIMPLE, interp=interp)
+        info = mlbm.stencils_info(st)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
+        variant, ms = mlbm.autotune(ctx, 10, flush_l2=True)
+        per_node = 4 * 18 + (32 if interp == mlbm.INTERP_RBF else 24) * K + 4 * K + 1
+        alg = info["n_wls"] * per_node + info["n_lagrange"] * (4 * 18 + 4 * 12 + 4 + 1) + info["n_eq"] * (16 + 36 + 1)
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
+        mlbm.set_kernel_variant(ctx, variant)
+        cd, cl = np.empty(args.steps // every), np.empty(args.steps // every)
+        for i in range(len(cd)):
+            mlbm.step(ctx, every)
+            _, _, cd[i], cl[i] = mlbm.drag_lift(ctx, d, u0)
+        h = len(cd) // 2
+        out[name] = {"K": K, "variant": variant, "us_per_step_flushed": ms * 1e3, "mnups": w.n / (ms * 1e3),
+                     "algorithmic_bytes_per_step": int(alg),
+                     "hbm_frac_of_measured_peak": alg / (ms * 1e-3) / 1e9 / peak,
+                     "strouhal": _strouhal(cl[h:], every, d / s_, u0), "cd_mean": float(np.mean(cd[h:])),
+                     "cl_amplitude": float(np.ptp(cl[h:]) / 2)}
+        print(json.dumps(out[name]), file=sys.stderr, flush=True)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -505,6 +548,8 @@ def main():
     po = sub.add_parser("porous")
     po.add_argument("--nodes", type=int, default=1_000_000)
     po.add_argument("--areas", default="voronoi", choices=["uniform", "voronoi"])
+    rb = sub.add_parser("rbf")
+    rb.add_argument("--steps", type=int, default=200_000)
     lb = sub.add_parser("lbm")
     lb.add_argument("--steps", type=int, default=200_000)
     lb.add_argument("--areas", default="voronoi", choices=["spacing", "voronoi"])
@@ -516,6 +561,8 @@ def main():
         hybrid_study(args)
     elif args.cmd == "lbm":
         lbm_study(args)
+    elif args.cmd == "rbf":
+        rbf_study(args)
     elif args.cmd == "porous":
         porous_study(args)
     elif args.cmd == "batch":

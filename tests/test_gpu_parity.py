@@ -101,6 +101,55 @@ def test_bgk_steps_match_oracle_elementwise(case, variant):
         assert err < pop_tol(done), (case, done, err)
 
 
+@pytest.mark.parametrize("variant", [0, 10, 11, 12])
+@pytest.mark.parametrize("case", ["jittered", "karman_small", "karman_hybrid_small", "porous_small"])
+def test_rbf_steps_match_oracle_elementwise(case, variant):
+    """RBF-FD stencils (the paper's interpolant, Sec. 2.2): the GPU step against
+    the oracle's step with its own RBF-FD weights, 10 steps from a random state."""
+    if case == "jittered":
+        w, K, s, bb, tau, g = I.jittered_periodic(37, 29, 0.25, seed=4), 16, 0.8, 1, 0.75, (1e-5, 3e-6)
+    elif case == "karman_small":
+        w, K, s, bb, tau, g = I.karman(seed=2, scale=0.25), 16, 0.5, 0, 0.62, (0.0, 0.0)
+    elif case == "karman_hybrid_small":
+        w, K, s, bb, tau, g = I.karman(seed=2, scale=0.25, lattice_beyond_d=1.0), 24, 0.5, 0, 0.62, (0.0, 0.0)
+    else:
+        w, K, s, bb, tau, g = I.porous(seed=5, n_target=15000), 16, 0.5, 1, 0.8, (1e-5, 0.0)
+    st = mlbm.build_stencils_for(w, K=K, s=s, bb_mode=bb, interp=mlbm.INTERP_RBF)
+    ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, *g))
+    mlbm.set_kernel_variant(ctx, variant)
+    f0 = to_f32_state(random_populations(w.n, 11))
+    mlbm.set_populations(ctx, f0)
+    op = O.Operator(w, K=K, s=s, bb_mode=bb, interp="rbf").check()
+    f = f0
+    done = 0
+    for n_steps in (1, 9):
+        mlbm.step(ctx, n_steps)
+        for _ in range(n_steps):
+            f = O.bgk_step(op, f, tau, g)
+        done += n_steps
+        err = np.abs(mlbm.get_populations(ctx) - f).max()
+        assert err < pop_tol(done), (case, done, err)
+    fx, fy, _, _ = mlbm.drag_lift(ctx, 1.0, 1.0)
+    ox, oy = O.force_bgk(op, mlbm.get_populations(ctx))
+    assert abs(fx - ox) <= 1e-4 * max(abs(ox), 1e-12) + 1e-9 and abs(fy - oy) <= 1e-4 * max(abs(ox), 1e-12) + 1e-9
+
+
+def test_rbf_poiseuille_2000_steps_matches_oracle():
+    w = I.poiseuille_channel(40, 50, 0.2, seed=1)
+    g = (1e-6, 0.0)
+    st = mlbm.build_stencils_for(w, K=12, s=1.0, bb_mode=1, interp=mlbm.INTERP_RBF)
+    ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, 0.8, 0.0, *g))
+    mlbm.step(ctx, 2000)
+    _, u = mlbm.macroscopics(ctx)
+    op = O.Operator(w, K=12, s=1.0, bb_mode=1, interp="rbf").check()
+    f = O.run_bgk(op, O.equilibrium(np.ones(w.n), 0, 0), 0.8, g, 2000)
+    _, ux, uy = O.macroscopics(f, g)
+    err = np.linalg.norm(np.stack([u[:, 0] - ux, u[:, 1] - uy])) / np.linalg.norm(np.stack([ux, uy]))
+    assert err <= 1e-5, err
+    with pytest.raises(mlbm.MlbmError):
+        mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, *g))
+
+
 def test_regular_lattice_streaming_is_exact_in_fp32():
     """s = h on a regular lattice: the Lagrange weights are exactly one-hot, so
     with tau = 1 and no force the GPU step is the index shift of Eq. (1) followed
