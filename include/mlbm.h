@@ -129,8 +129,8 @@ mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_geometry* ge
  * of an interpolated bounce-back link) solve the (K+6)-square saddle-point
  * system in FP64 (LU, partial pivoting); they are stored per direction, 8 K
  * FP32 weights per node.  Lagrange blocks and simple bounce-back are as for
- * the least-squares fit.  RBF-FD stencils serve BGK contexts (mlbm_init
- * returns MLBM_E_INVALID for the tau = 1 model with them).  Errors: as
+ * the least-squares fit.  Both collision models use them (the tau = 1 model
+ * interpolates rho and u with the same per-direction weights).  Errors: as
  * mlbm_build_stencils; a singular RBF-FD system gives
  * MLBM_E_SINGULAR_STENCIL.
  */

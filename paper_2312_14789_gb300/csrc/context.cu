@@ -181,8 +181,6 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     const int64_t n = H.n, np = c->n_pad;
     const int K = H.K, Kq = K / 4;
     // ---- host-side device layout
-    if (H.interp == MLBM_INTERP_RBF && p->model != MLBM_MODEL_BGK)
-        return set_error(MLBM_E_INVALID, "init: RBF-FD stencils serve the BGK model only");
     const bool rbf = H.interp == MLBM_INTERP_RBF;
     std::vector<int32_t> hidx((size_t)Kq * np * 4, 0);
     std::vector<float> hM((size_t)6 * Kq * np * 4, 0.f);

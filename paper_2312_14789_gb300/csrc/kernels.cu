@@ -479,7 +479,9 @@ __global__ void __launch_bounds__(256, MINB) bgk_split_persistent(Stencil S, con
     }
 }
 
-template <int KQ, int LPN>
+// RBF = true (one lane per node): the least-squares-kind nodes take each
+// direction's (dr, u, v) increment from their stored RBF-FD weights
+template <int KQ, int LPN, bool RBF = false>
 __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __restrict__ in, float4* __restrict__ out,
                                           const Collide& C0, int p, int h, unsigned grp) {
     const Collide C = collide_of(S, C0, p);
@@ -492,8 +494,34 @@ __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __rest
     const float4 me = __ldg(in + p);
     float c[3][6];
     float4 v9[9];
+    float dd[RBF ? 8 : 1][3];  // RBF-FD increments per direction
     float r = 0.f, cx = 0.f, cy = 0.f;
-    if (kind == 0) {
+    if (kind == 0 && RBF) {
+#pragma unroll
+        for (int k = 0; k < (RBF ? 8 : 1); ++k) dd[k][0] = dd[k][1] = dd[k][2] = 0.f;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+            float wt[8][4];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float4 w4 = ld_stream(S.Wr + (size_t)(k * KQ + q) * S.n_pad + p);
+                wt[k][0] = w4.x; wt[k][1] = w4.y; wt[k][2] = w4.z; wt[k][3] = w4.w;
+            }
+            const int ids[4] = {id.x, id.y, id.z, id.w};
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const float4 rv = __ldg(in + ids[cc]);
+                const float vx = rv.x - me.x, vy = rv.y - me.y, vz = rv.z - me.z;
+#pragma unroll
+                for (int k = 0; k < (RBF ? 8 : 1); ++k) {
+                    dd[k][0] = fmaf(wt[k][cc], vx, dd[k][0]);
+                    dd[k][1] = fmaf(wt[k][cc], vy, dd[k][1]);
+                    dd[k][2] = fmaf(wt[k][cc], vz, dd[k][2]);
+                }
+            }
+        }
+    } else if (kind == 0) {
 #pragma unroll
         for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -560,7 +588,13 @@ __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __rest
         float d[3] = {0.f, 0.f, 0.f};  // increments over the node's own (dr, u, v)
         if (!(is_link && S.bb_mode == 0)) {
             const float tt = is_link ? L.t[k - 1] : -1.0f;
-            if (kind == 0) {
+            if (kind == 0 && RBF) {
+                // the stored row is at the departure point, or at the reflected
+                // point of an interpolated bounce-back link
+                d[0] = dd[RBF ? k - 1 : 0][0];
+                d[1] = dd[RBF ? k - 1 : 0][1];
+                d[2] = dd[RBF ? k - 1 : 0][2];
+            } else if (kind == 0) {
                 float pb[6];
                 basis_at(k, tt, pb);
                 eval_coeffs(c, pb, d);
@@ -606,6 +640,29 @@ __global__ void __launch_bounds__(256, MINB) tau1_step_kernel(Stencil S, const f
     const unsigned lane = threadIdx.x & 31u;
     const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
     tau1_node<KQ, LPN>(S, in, out, C, p, h, grp);
+}
+
+template <int KQ, int MINB>
+__global__ void __launch_bounds__(256, MINB) tau1_step_rbf(Stencil S, const float4* __restrict__ in,
+                                                           float4* __restrict__ out, Collide C) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.n) return;
+    tau1_node<KQ, 1, true>(S, in, out, C, p, 0, 1u << (threadIdx.x & 31u));
+}
+
+template <int KQ, int MINB>
+__global__ void __launch_bounds__(256, MINB) tau1_step_rbf_persistent(Stencil S, const float4* __restrict__ in,
+                                                                      float4* __restrict__ out, Collide C, int dist) {
+    constexpr int TN = 256;
+    const int n_tiles = (S.n + TN - 1) / TN;
+    const unsigned lane = threadIdx.x & 31u;
+    if (threadIdx.x < 32)
+        for (int d = 0; d < dist; ++d) prefetch_tile_rbf<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (threadIdx.x < 32) prefetch_tile_rbf<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
+        const int p = tile * TN + threadIdx.x;
+        if (p < S.n) tau1_node<KQ, 1, true>(S, in, out, C, p, 0, 1u << lane);
+    }
 }
 
 template <int KQ, int LPN, int MINB>
@@ -791,6 +848,20 @@ __global__ void __launch_bounds__(128) force_kernel(Stencil S, int model, int n_
                 if (S.bb_mode == 0) {
                     const float4 me = ruv[p];
                     d[0] = me.x; d[1] = me.y; d[2] = me.z;
+                } else if (kind == 0 && S.Wr) {
+                    d[0] = d[1] = d[2] = 0.f;
+                    for (int q = 0; q < KQ; ++q) {
+                        const int4 id = S.idx[(size_t)q * S.n_pad + p];
+                        const float4 wq = S.Wr[(size_t)((k - 1) * KQ + q) * S.n_pad + p];
+                        const int ids[4] = {id.x, id.y, id.z, id.w};
+                        const float ws[4] = {wq.x, wq.y, wq.z, wq.w};
+                        for (int cq = 0; cq < 4; ++cq) {
+                            const float4 v = ruv[ids[cq]];
+                            d[0] = fmaf(ws[cq], v.x, d[0]);
+                            d[1] = fmaf(ws[cq], v.y, d[1]);
+                            d[2] = fmaf(ws[cq], v.z, d[2]);
+                        }
+                    }
                 } else if (kind == 0) {
                     float pb[6];
                     basis_at(k, L.t[k - 1], pb);
@@ -1053,6 +1124,19 @@ cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* ou
                              cudaStream_t st) {
     if (S.n == 0) return cudaSuccess;
     const int block = 256;
+    if (S.Wr) {
+        // RBF-FD stencils: variants map as for the BGK step
+        if (variant == 10) {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_rbf_persistent<KQC, 1>, 256, S.n, st, [&](int g) { dev::tau1_step_rbf_persistent<KQC, 1><<<g, block, 0, st>>>(S, in, out, C, 1); })));
+        } else if (variant == 12) {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_rbf_persistent<KQC, 2>, 256, S.n, st, [&](int g) { dev::tau1_step_rbf_persistent<KQC, 2><<<g, block, 0, st>>>(S, in, out, C, 1); })));
+        } else if (variant == 0) {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_rbf<KQC, 1><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C)));
+        } else {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_rbf<KQC, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C)));
+        }
+        return cudaGetLastError();
+    }
     switch (variant) {
         case 0: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 1, 1><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
         case 1: MLBM_DISPATCH_KQ(S.Kq, (dev::tau1_step_kernel<KQC, 2, 1><<<blocks_for(2 * (int64_t)S.n, block), block, 0, st>>>(S, in, out, C))); break;

@@ -146,8 +146,29 @@ def test_rbf_poiseuille_2000_steps_matches_oracle():
     _, ux, uy = O.macroscopics(f, g)
     err = np.linalg.norm(np.stack([u[:, 0] - ux, u[:, 1] - uy])) / np.linalg.norm(np.stack([ux, uy]))
     assert err <= 1e-5, err
-    with pytest.raises(mlbm.MlbmError):
-        mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, *g))
+
+
+@pytest.mark.parametrize("variant", [0, 11, 12])
+def test_rbf_tau1_steps_match_oracle(variant):
+    """tau = 1 (MLBM1) with RBF-FD stencils on a porous box with interpolated
+    bounce-back: 10 steps from a random (rho, u) against the oracle."""
+    w = I.porous(seed=5, n_target=15000)
+    g = (1e-5, 0.0)
+    st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=1, interp=mlbm.INTERP_RBF)
+    ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, *g))
+    mlbm.set_kernel_variant(ctx, variant)
+    rng = np.random.default_rng(4)
+    ru = np.stack([1 + (0.01 * rng.standard_normal(w.n)).astype(np.float32).astype(np.float64),
+                   (0.01 * rng.standard_normal(w.n)).astype(np.float32).astype(np.float64),
+                   (0.01 * rng.standard_normal(w.n)).astype(np.float32).astype(np.float64)], 1)
+    mlbm.set_fields(ctx, ru)
+    op = O.Operator(w, K=16, s=0.5, bb_mode=1, interp="rbf").check()
+    a = ru
+    for _ in range(10):
+        a = O.mlbm1_step(op, a, g)
+    mlbm.step(ctx, 10)
+    b = mlbm.get_fields(ctx)
+    assert np.abs(b - a).max() < 5 * pop_tol(10)
 
 
 def test_regular_lattice_streaming_is_exact_in_fp32():
