@@ -194,6 +194,23 @@ def run_reference(args, rank, world):
     }))
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the job's time is its slowest
+    rank's); the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(nodes_per_rank, steps, world, ms):
+    """Mnode-updates/s of the whole job: every rank advances its own replica
+    of the workload (weak scaling), timed by the slowest rank."""
+    return nodes_per_rank * steps * world / (ms / 1e3) / 1e6
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2312_14789_gb300 import mlbm
@@ -230,13 +247,10 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    total_ms = float(e0.elapsed_time(e1))
+    total_ms = max_over_ranks(float(e0.elapsed_time(e1)), dist, "cuda")
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    value = n * args.steps * world / (total_ms / 1e3) / 1e6
+    value = whole_job_rate(n, args.steps, world, total_ms)
 
     # end to end through the public API with host buffers: upload the state
     # of all six runs from pinned memory, advance, read the fields and the
