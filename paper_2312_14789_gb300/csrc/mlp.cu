@@ -122,10 +122,10 @@ __device__ __forceinline__ void load_x(const float* __restrict__ X, int64_t src0
 }
 
 // one hidden layer: A (k-tiles of the input) -> ReLU(A W + b) packed as the
-// next A fragments; z (optional) receives the FP32 accumulators
+// next A fragments
 template <int KT>
 __device__ __forceinline__ void hidden_layer(const uint32_t (*a)[4], const __nv_bfloat16* wt, int stride,
-                                             const float* bias, int g, int t, uint32_t (*out)[4], float (*z)[4]) {
+                                             const float* bias, int g, int t, uint32_t (*out)[4]) {
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const float bl = bias[8 * nt + 2 * t], bh = bias[8 * nt + 2 * t + 1];
@@ -135,9 +135,6 @@ __device__ __forceinline__ void hidden_layer(const uint32_t (*a)[4], const __nv_
             const __nv_bfloat16* w = wt + (8 * nt + g) * stride + 16 * kt + 2 * t;
             mma(d, a[kt], ld32(w), ld32(w + 8));
         }
-        if (z)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) z[nt][i] = d[i];
         const float r0 = fmaxf(d[0], 0.f), r1 = fmaxf(d[1], 0.f), r2 = fmaxf(d[2], 0.f), r3 = fmaxf(d[3], 0.f);
         out[nt >> 1][(nt & 1) * 2 + 0] = pack2(r0, r1);
         out[nt >> 1][(nt & 1) * 2 + 1] = pack2(r2, r3);
@@ -165,9 +162,9 @@ __global__ void __launch_bounds__(128) forward_kernel(const float* __restrict__ 
         const int64_t row0 = tile * 16;
         uint32_t a1[1][4], a2[4][4], a3[4][4], a4[4][4];
         load_x(X, row0 + g < n ? row0 + g : -1, row0 + g + 8 < n ? row0 + g + 8 : -1, t, a1[0]);
-        hidden_layer<1>(a1, s.wt1, kS16, s.b1, g, t, a2, nullptr);
-        hidden_layer<4>(a2, s.wt2, kS64, s.b2, g, t, a3, nullptr);
-        hidden_layer<4>(a3, s.wt3, kS64, s.b3, g, t, a4, nullptr);
+        hidden_layer<1>(a1, s.wt1, kS16, s.b1, g, t, a2);
+        hidden_layer<4>(a2, s.wt2, kS64, s.b2, g, t, a3);
+        hidden_layer<4>(a3, s.wt3, kS64, s.b3, g, t, a4);
         float d[4];
         output_layer(a4, s, g, t, d);
         // this lane holds output columns 2t, 2t + 1 of rows g, g + 8
@@ -307,9 +304,9 @@ __global__ void __launch_bounds__(128) grad_kernel(const float* __restrict__ P, 
         const int64_t src0 = r0 < n ? data_row(r0, n_data, seed, step) : -1;
         const int64_t src1 = r1 < n ? data_row(r1, n_data, seed, step) : -1;
         load_x(X, src0, src1, t, a1[0]);
-        hidden_layer<1>(a1, s.f.wt1, kS16, s.f.b1, g, t, a2, nullptr);
-        hidden_layer<4>(a2, s.f.wt2, kS64, s.f.b2, g, t, a3, nullptr);
-        hidden_layer<4>(a3, s.f.wt3, kS64, s.f.b3, g, t, a4, nullptr);
+        hidden_layer<1>(a1, s.f.wt1, kS16, s.f.b1, g, t, a2);
+        hidden_layer<4>(a2, s.f.wt2, kS64, s.f.b2, g, t, a3);
+        hidden_layer<4>(a3, s.f.wt3, kS64, s.f.b3, g, t, a4);
         float y[4];
         output_layer(a4, s.f, g, t, y);
         // ---- output error dY = 2 (Y - T) / n (zero on padding rows and
