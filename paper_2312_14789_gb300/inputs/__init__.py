@@ -236,7 +236,8 @@ def poiseuille_channel(nx: int = 40, ny: int = 50, jitter: float = 0.2, seed: in
 def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: float = 4.1,
            center_d: tuple = (2.0, 2.0), U0: float = 0.05, r_fine: float = 0.37, r_coarse: float = 0.74,
            fine_band_d: float = 1.5, blend_to_d: float = 4.0, scale: float = 1.0,
-           lattice_beyond_d: float | None = None, areas: str = "voronoi") -> Workload:
+           lattice_beyond_d: float | None = None, areas: str = "voronoi",
+           coarse_beyond_d: float | None = None, coarse_h: int = 2) -> Workload:
     """Channel length_d*D x height_d*D with a solid cylinder of diameter D.
 
     Lengths are in units of the reference spacing h_ref=1, so D is the number
@@ -257,7 +258,17 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     scattered refinement fills the rest, its radius blended from r_fine
     (within min(fine_band_d, lattice_beyond_d/2)*D) to r_coarse at the
     lattice.  Requires r_coarse > 1/sqrt(2), so
-    that no scattered node fits between lattice points."""
+    that no scattered node fits between lattice points.
+
+    coarse_beyond_d (with lattice_beyond_d; the coarsened hybrid set of
+    Sec. 3.1): beyond coarse_beyond_d*D from the surface only the lattice
+    points whose coordinates are multiples of coarse_h remain (the sampling
+    radius there is 0.75 coarse_h, so no scattered node fills the holes).
+
+    areas: "voronoi" (default) gives each node the fluid part of its Voronoi
+    cell (rastered), which weights the wall nodes on the cylinder surface by
+    the half-cells they own; "spacing" gives each node the square of its
+    local sampling radius, normalised to the fluid area."""
     D = D * scale
     lx, ly = length_d * D, height_d * D
     cx, cy, R = center_d[0] * D, center_d[1] * D, 0.5 * D
@@ -271,6 +282,10 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
         fine_band_d = min(fine_band_d, 0.5 * lattice_beyond_d)
     t = np.clip((dist - fine_band_d * D) / ((blend_to_d - fine_band_d) * D), 0.0, 1.0)
     rgrid = r_fine + t * (r_coarse - r_fine)
+    if coarse_beyond_d is not None:
+        if lattice_beyond_d is None or coarse_beyond_d <= lattice_beyond_d:
+            raise ValueError("coarsening needs a hybrid set with coarse_beyond_d > lattice_beyond_d")
+        rgrid = np.where(dist > coarse_beyond_d * D, 0.75 * coarse_h, rgrid)
     # equilibrium nodes on the four sides
     hb = r_coarse * 1.19
     if lattice_beyond_d is not None:
@@ -296,7 +311,11 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
     if lattice_beyond_d is not None:
         gx_, gy_ = np.meshgrid(np.arange(1, int(lx)), np.arange(1, int(ly)), indexing="xy")
         lat = np.stack([gx_.ravel(), gy_.ravel()], 1).astype(np.float64)
-        far = np.hypot(lat[:, 0] - cx, lat[:, 1] - cy) - R > lattice_beyond_d * D
+        dlat = np.hypot(lat[:, 0] - cx, lat[:, 1] - cy) - R
+        far = dlat > lattice_beyond_d * D
+        if coarse_beyond_d is not None:
+            on_coarse = (np.mod(lat[:, 0], coarse_h) == 0) & (np.mod(lat[:, 1], coarse_h) == 0)
+            far &= (dlat <= coarse_beyond_d * D) | on_coarse
         pre.append(lat[far])
     pts = _sample((0.0, 0.0, lx, ly), (0, 0), rgrid, np.array([[cx, cy, R]]), 0.5,
                   np.concatenate(pre, 0), seed,
@@ -324,11 +343,12 @@ def karman(seed: int = 2, D: float = 40.0, length_d: float = 22.0, height_d: flo
         area = r_at ** 2
         area *= (lx * ly - np.pi * R * R) / area.sum()
     name = f"karman_D{D:g}_s{seed}" + ("" if lattice_beyond_d is None else f"_hybrid{lattice_beyond_d:g}") + \
+        ("" if coarse_beyond_d is None else f"_coarse{coarse_beyond_d:g}x{coarse_h}") + \
         ("" if areas == "spacing" else "_" + areas)
     return Workload(name, pts, cls, (0.0, 0.0, lx, ly), (OPEN,) * 4,
                     np.array([[cx, cy, R]]), eqv, area, 1.0,
                     {"D": D, "U0": U0, "H": ly, "L": lx, "seed": seed, "n_eq": nf, "n_wall": m,
-                     "lattice_beyond_d": lattice_beyond_d})
+                     "lattice_beyond_d": lattice_beyond_d, "coarse_beyond_d": coarse_beyond_d})
 
 
 # --------------------------------------------------------------------------

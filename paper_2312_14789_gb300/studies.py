@@ -417,7 +417,8 @@ def lbm_study(args):
     GB300: the vortex street at Re = 100 on the regular lattice with D = 80
     spacings (the lattice resolution of the meshless run with D = 40 node
     spacings and s = 1/2, so both take the same time step) against the
-    meshless step on the scattered and the hybrid node sets.  Per method:
+    meshless step on the scattered, the hybrid and the coarsened hybrid
+    (spacing 2 beyond 2 D) node sets.  Per method:
     nodes, time per step (CUDA events, back to back), algorithmic bytes per
     step, Strouhal number and mean drag over the second half of --steps."""
     import torch
@@ -462,7 +463,9 @@ def lbm_study(args):
     print(json.dumps(out["lattice"]), file=sys.stderr, flush=True)
     # meshless on the scattered and the hybrid node sets
     for name, w in (("meshless_scattered", I.karman(seed=2, areas=args.areas)),
-                    ("meshless_hybrid", I.karman(seed=2, lattice_beyond_d=1.0, areas=args.areas))):
+                    ("meshless_hybrid", I.karman(seed=2, lattice_beyond_d=1.0, areas=args.areas)),
+                    ("meshless_hybrid_coarse", I.karman(seed=2, lattice_beyond_d=1.0, coarse_beyond_d=2.0,
+                                                        areas=args.areas))):
         st = mlbm.build_stencils_for(w, K=16, s=s_, bb_mode=mlbm.BB_SIMPLE)
         info = mlbm.stencils_info(st)
         ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
@@ -481,7 +484,7 @@ def lbm_study(args):
                      "strouhal": _strouhal(cl[h:], every, d_lb, u0), "cd_mean": float(np.mean(cd[h:])),
                      "cl_amplitude": float(np.ptp(cl[h:]) / 2)}
         print(json.dumps(out[name]), file=sys.stderr, flush=True)
-    for name in ("meshless_scattered", "meshless_hybrid"):
+    for name in ("meshless_scattered", "meshless_hybrid", "meshless_hybrid_coarse"):
         out[name]["time_per_step_over_lattice"] = out[name]["us_per_step"] / out["lattice"]["us_per_step"]
     print(json.dumps(out))
 

@@ -70,7 +70,7 @@ def test_poiseuille_channel_2000_steps_matches_oracle():
 
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("case", ["lattice", "channel_halfway", "jittered", "karman_small", "karman_hybrid_small",
-                                  "porous_small"])
+                                  "karman_coarse_small", "porous_small"])
 def test_bgk_steps_match_oracle_elementwise(case, variant):
     if case == "lattice":
         w, K, s, bb, tau, g = I.lattice(33, 17), 12, 1.0, 1, 0.7, (1e-5, -2e-6)
@@ -82,6 +82,9 @@ def test_bgk_steps_match_oracle_elementwise(case, variant):
         w, K, s, bb, tau, g = I.karman(seed=2, scale=0.25), 16, 0.5, 0, 0.62, (0.0, 0.0)
     elif case == "karman_hybrid_small":
         w, K, s, bb, tau, g = I.karman(seed=2, scale=0.25, lattice_beyond_d=1.0), 16, 0.5, 0, 0.62, (0.0, 0.0)
+    elif case == "karman_coarse_small":
+        w = I.karman(seed=2, scale=0.25, lattice_beyond_d=1.0, coarse_beyond_d=2.0)
+        K, s, bb, tau, g = 16, 0.5, 0, 0.62, (0.0, 0.0)
     else:
         w, K, s, bb, tau, g = I.porous(seed=5, n_target=15000), 16, 0.5, 1, 0.8, (1e-5, 0.0)
     f0 = to_f32_state(random_populations(w.n, 11))
