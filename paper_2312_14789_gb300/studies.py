@@ -6,6 +6,7 @@
     python -m paper_2312_14789_gb300.studies porous [--nodes 1000000]
     python -m paper_2312_14789_gb300.studies lbm [--steps 200000]
     python -m paper_2312_14789_gb300.studies rbf [--steps 200000]
+    python -m paper_2312_14789_gb300.studies kernels [--nodes 1000000]
 
 batch: 64 porous samples (seeds 1000..1063) with node counts U(50k, 400k),
 porosity U(0.5, 0.85) and a mix of Darcy (s = 1) and inertial (s = 1/2, 1/4)
@@ -531,6 +532,56 @@ def rbf_study(args):
     print(json.dumps(out))
 
 
+def _alg_bytes(info, K, model):
+    """Bytes one step must move at minimum, by node kind.  BGK: least-squares
+    node 4 (9 + 9) + 24 K + 4 K + 1, Lagrange node 4 (9 + 9) + 48 + 4 + 1,
+    equilibrium node 16 + 36 + 1.  tau = 1 (state (rho - 1, u, v) padded to
+    16 B): least-squares node 16 + 16 + 24 K + 4 K + 1, Lagrange node
+    16 + 16 + 48 + 4 + 1, equilibrium node 16 + 16 + 1."""
+    pops = 32 if model == 1 else 72
+    wls = pops + 28 * K + 1
+    lag = pops + 48 + 4 + 1
+    eq = 16 + (16 if model == 1 else 36) + 1
+    return info["n_wls"] * wls + info["n_lagrange"] * lag + info["n_eq"] * eq
+
+
+def kernels_study(args):
+    """Step throughput on single workloads, each autotuned over the kernel
+    variants with the L2 flushed before every timed step: one vortex-street
+    run (BGK, K = 16, s = 1/2, simple bounce-back), the ~1M-node porous box
+    under tau = 1 and under BGK (K = 16, s = 1/2, interpolated bounce-back,
+    and BGK with simple bounce-back to show what the interpolated links cost).
+    Reports the best variant, microseconds per step, node-updates/s and the
+    fraction of the measured HBM copy bandwidth reached by the algorithmic
+    bytes."""
+    from paper_2312_14789_gb300 import inputs as I
+    from paper_2312_14789_gb300 import mlbm
+    sys.path.insert(0, ROOT)
+    import bench
+
+    peak = bench.peaks()[0]["hbm_gbs"]
+    wk = I.karman(seed=2)
+    wp = I.porous(seed=3, n_target=args.nodes, porosity=0.7)
+    cases = (("karman_one_bgk", wk, mlbm.BB_SIMPLE, mlbm.MODEL_BGK, 0.62, 0.0),
+             ("porous_tau1", wp, mlbm.BB_INTERPOLATED, mlbm.MODEL_TAU1, 1.0, 1e-6),
+             ("porous_bgk", wp, mlbm.BB_INTERPOLATED, mlbm.MODEL_BGK, 0.8, 1e-6),
+             ("porous_bgk_simple_bb", wp, mlbm.BB_SIMPLE, mlbm.MODEL_BGK, 0.8, 1e-6))
+    out = {"study": "kernels", "peak_hbm_gbs": peak, "runs": []}
+    for name, w, bb, model, tau, g in cases:
+        st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=bb)
+        info = mlbm.stencils_info(st)
+        ctx = mlbm.init(st, mlbm.Params(model, tau, 0.0, g, 0.0))
+        variant, ms = mlbm.autotune(ctx, args.steps, flush_l2=True)
+        alg = _alg_bytes(info, 16, model)
+        out["runs"].append({"workload": name, "nodes": int(w.n), "n_link_nodes": int(info["n_link_nodes"]),
+                            "n_links": int(info["n_links"]), "variant": variant, "us_per_step": ms * 1e3,
+                            "mnups": w.n / (ms * 1e3), "algorithmic_bytes_per_step": int(alg),
+                            "hbm_frac_of_measured_peak": alg / (ms * 1e-3) / 1e9 / peak})
+        print(json.dumps(out["runs"][-1]), file=sys.stderr, flush=True)
+        del ctx
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -556,11 +607,16 @@ def main():
     lb = sub.add_parser("lbm")
     lb.add_argument("--steps", type=int, default=200_000)
     lb.add_argument("--areas", default="voronoi", choices=["spacing", "voronoi"])
+    kn = sub.add_parser("kernels")
+    kn.add_argument("--nodes", type=int, default=1_000_000)
+    kn.add_argument("--steps", type=int, default=20)
     hb = sub.add_parser("hybrid")
     hb.add_argument("--steps", type=int, default=200_000)
     hb.add_argument("--lattice-d", type=float, default=1.0)
     args = ap.parse_args()
-    if args.cmd == "hybrid":
+    if args.cmd == "kernels":
+        kernels_study(args)
+    elif args.cmd == "hybrid":
         hybrid_study(args)
     elif args.cmd == "lbm":
         lbm_study(args)
