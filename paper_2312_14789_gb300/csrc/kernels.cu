@@ -54,11 +54,17 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
         const float4 ob = __ldg(f8in + 2 * (size_t)p + 1);
         if (kind == 0 && RBF) {
             // f_k(x) = own_k + sum_j w_kj (f_k(j) - own_k), weights per direction
+            int4 idv[(KQ + LPN - 1) / LPN];
+#pragma unroll
+            for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
+                const int q = i * LPN + h;
+                if (q < KQ) idv[i] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+            }
 #pragma unroll
             for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
                 const int q = i * LPN + h;
                 if (q < KQ) {
-                    const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                    const int4 id = idv[i];
                     float wt[8][4];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
@@ -82,11 +88,19 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
                 }
             }
         } else if (kind == 0) {
+            // all index rows first, so the gathers of later stencil quads need
+            // not wait for their index load behind the matrix rows
+            int4 idv[(KQ + LPN - 1) / LPN];
+#pragma unroll
+            for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
+                const int q = i * LPN + h;
+                if (q < KQ) idv[i] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+            }
 #pragma unroll
             for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
                 const int q = i * LPN + h;
                 if (q < KQ) {
-                    const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                    const int4 id = idv[i];
                     float4 m[6];
 #pragma unroll
                     for (int a = 0; a < 6; ++a) m[a] = ld_stream(S.M + (size_t)(a * KQ + q) * S.n_pad + p);
@@ -499,9 +513,12 @@ __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __rest
     if (kind == 0 && RBF) {
 #pragma unroll
         for (int k = 0; k < (RBF ? 8 : 1); ++k) dd[k][0] = dd[k][1] = dd[k][2] = 0.f;
+        int4 idv[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) idv[q] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
 #pragma unroll
         for (int q = 0; q < KQ; ++q) {
-            const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+            const int4 id = idv[q];
             float wt[8][4];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -526,11 +543,17 @@ __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __rest
         for (int f = 0; f < 3; ++f)
 #pragma unroll
             for (int a = 0; a < 6; ++a) c[f][a] = 0.f;
+        int4 idv[(KQ + LPN - 1) / LPN];
+#pragma unroll
+        for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
+            const int q = i * LPN + h;
+            if (q < KQ) idv[i] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+        }
 #pragma unroll
         for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
             const int q = i * LPN + h;
             if (q < KQ) {
-                const int4 id = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                const int4 id = idv[i];
                 float4 m[6];
 #pragma unroll
                 for (int a = 0; a < 6; ++a) m[a] = ld_stream(S.M + (size_t)(a * KQ + q) * S.n_pad + p);

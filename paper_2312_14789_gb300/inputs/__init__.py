@@ -431,6 +431,37 @@ def porous(seed: int = 3, n_target: int = 1_000_000, porosity: float = 0.7, rmin
                      "mean_d": float(2 * disks[:, 2].mean()) if len(disks) else 0.0})
 
 
+def cylinder_array(side: float = 40.0, radius: float = 8.0, h: float = 1.0, seed: int = 0,
+                   r_pd: float = 0.84, areas: str = "voronoi") -> Workload:
+    """One solid disk of the given radius at the centre of a doubly periodic
+    square cell of the given side: a square array of cylinders with solid
+    area fraction c = pi r^2 / side^2.  Wall nodes sit on the circle (arc
+    spacing about h); fluid nodes are Poisson-disk samples of radius r_pd*h.
+    areas: "voronoi" (fluid part of each node's Voronoi cell, rastered at
+    0.2h) or "uniform"."""
+    rng = np.random.default_rng(seed)
+    c = side / 2.0
+    disks = np.array([[c, c, radius]])
+    m = max(8, int(round(2 * np.pi * radius / h)))
+    a = rng.uniform(0, 2 * np.pi) + 2 * np.pi * np.arange(m) / m
+    fixed = np.stack([c + radius * np.cos(a), c + radius * np.sin(a)], 1)
+    density = 0.68 / (r_pd * h) ** 2
+    box = (0.0, 0.0, side, side)
+    pts = _sample(box, (1, 1), np.full((2, 2), r_pd * h), disks, 0.25, fixed, seed,
+                  max_out=int(2.0 * side * side * density) + m + 1000)
+    n = len(pts)
+    cls = np.zeros(n, np.uint8)
+    cls[:m] = WALL
+    fluid_area = side * side - np.pi * radius ** 2
+    if areas == "voronoi":
+        area = fluid_voronoi_areas(pts, box, (True, True), disks, 0.2 * h)
+    else:
+        area = np.full(n, fluid_area / n)
+    return Workload(f"cylarray_L{side:g}_r{radius:g}_s{seed}", pts, cls, box,
+                    (PERIODIC, PERIODIC, PERIODIC, PERIODIC), disks, np.zeros((n, 3)), area, h,
+                    {"seed": seed, "solid_fraction": float(np.pi * radius ** 2 / side ** 2), "L": side})
+
+
 # --------------------------------------------------------------------------
 # Random arrays (initial perturbations, feature noise); no physics
 # --------------------------------------------------------------------------
