@@ -315,8 +315,9 @@ mlbm_status mlbm_set_kernel_variant(mlbm_ctx* ctx, int variant);
 int mlbm_kernel_variant(const mlbm_ctx* ctx);
 mlbm_status mlbm_autotune(mlbm_ctx* ctx, int steps_per_variant, double* best_ms);
 /* As mlbm_autotune; with flush_l2 != 0 every timed step is preceded by a
-   512 MiB device write (a temporary buffer) so that steps are timed with a
-   cold L2, and each step is timed on its own. */
+   read of a zeroed 512 MiB temporary device buffer, so that steps are timed
+   with a cold L2 that holds no dirty lines, and each step is timed on its
+   own.  Returns MLBM_E_OOM if the buffer cannot be allocated. */
 mlbm_status mlbm_autotune_ex(mlbm_ctx* ctx, int steps_per_variant, int flush_l2, double* best_ms);
 
 /* ------------------------------------------------------------------ batches */
