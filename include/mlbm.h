@@ -305,6 +305,14 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        capped for 2 / 3 resident blocks of 256, followed by a second kernel
  *        that recomputes every node with bounce-back links in full and
  *        overwrites its output (BGK only; tau = 1 runs variant 11)
+ *   20-21 as 11 (plain grid, capped for 2 blocks) and as 10 (persistent,
+ *        uncapped), with the first three index rows and the rest population
+ *        loaded before the node kind is read, so their latency overlaps the
+ *        meta load (BGK only; tau = 1 runs variant 11).  RBF-FD stencils map
+ *        10 and 12 to the persistent kernel (uncapped / capped for 2 blocks),
+ *        0 to the plain uncapped kernel, 20 and 21 to the plain capped and the
+ *        persistent uncapped kernel with the early loads, and the rest to the
+ *        plain kernel capped for 2 blocks
  * Variants 4 and up are available for K = 12, 16, 24 and 32.
  * The default is 12 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream

@@ -81,7 +81,7 @@ struct mlbm_ctx {
 
 namespace {
 constexpr int kGraphSteps = 16;
-constexpr int kMaxVariant = 19;  // step kernel variants 0..19 (see mlbm_set_kernel_variant)
+constexpr int kMaxVariant = 21;  // step kernel variants 0..21 (see mlbm_set_kernel_variant)
 }
 
 // Cold-cache start for timed steps: reading a zeroed buffer several times the

@@ -31,14 +31,27 @@ namespace dev {
 // q = h, h + LPN, ... and the partial sums are combined with a pair shuffle.
 // LINKS = false leaves out the bounce-back overrides (the split variants
 // recompute the nodes with links in a second pass); RBF = true interpolates
-// the least-squares-kind nodes with their stored RBF-FD weights
-template <int KQ, int LPN, bool LINKS = true, bool RBF = false>
+// the least-squares-kind nodes with their stored RBF-FD weights.  SPEC = true
+// loads the first three index rows and the rest population before the node
+// kind is known (they are read by every stencil kind), so they are in flight
+// together with the meta byte
+template <int KQ, int LPN, bool LINKS = true, bool RBF = false, bool SPEC = false>
 __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restrict__ f8in,
                                          const float* __restrict__ f0in, float4* __restrict__ f8out,
                                          float* __restrict__ f0out, const Collide& C0, int p, int h, unsigned grp) {
     const Collide C = collide_of(S, C0, p);
     const uint8_t meta = S.meta[p];
     const int kind = meta & 3;
+    int4 idv[(KQ + LPN - 1) / LPN];
+    float f0own = 0.f;
+    if (SPEC) {
+#pragma unroll
+        for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
+            const int q = i * LPN + h;
+            if (q < KQ && q < 3) idv[i] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+        }
+        f0own = f0in[p];
+    }
     float g[9];
     if (kind == 2) {
         const float4 e = S.eqv[p];
@@ -54,11 +67,10 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
         const float4 ob = __ldg(f8in + 2 * (size_t)p + 1);
         if (kind == 0 && RBF) {
             // f_k(x) = own_k + sum_j w_kj (f_k(j) - own_k), weights per direction
-            int4 idv[(KQ + LPN - 1) / LPN];
 #pragma unroll
             for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
                 const int q = i * LPN + h;
-                if (q < KQ) idv[i] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                if (q < KQ && (!SPEC || q >= 3)) idv[i] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
             }
 #pragma unroll
             for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
@@ -90,11 +102,10 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
         } else if (kind == 0) {
             // all index rows first, so the gathers of later stencil quads need
             // not wait for their index load behind the matrix rows
-            int4 idv[(KQ + LPN - 1) / LPN];
 #pragma unroll
             for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
                 const int q = i * LPN + h;
-                if (q < KQ) idv[i] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
+                if (q < KQ && (!SPEC || q >= 3)) idv[i] = ld_stream(S.idx + (size_t)q * S.n_pad + p);
             }
 #pragma unroll
             for (int i = 0; i < (KQ + LPN - 1) / LPN; ++i) {
@@ -177,7 +188,7 @@ __device__ __forceinline__ void bgk_node(const Stencil& S, const float4* __restr
                 }
             }
         }
-        g[0] = f0in[p];
+        g[0] = SPEC ? f0own : f0in[p];
 #pragma unroll
         for (int k = 1; k < 9; ++k) g[k] = acc[k - 1];
         collide_part<LPN>(g, C, h);
@@ -352,7 +363,7 @@ __device__ __forceinline__ void prefetch_tile(const Stencil& S, int base, int tn
     }
 }
 
-template <int KQ, int LPN, int MINB>
+template <int KQ, int LPN, int MINB, bool SPEC = false>
 __global__ void __launch_bounds__(256, MINB) bgk_step_kernel(Stencil S, const float4* __restrict__ f8in,
                                                              const float* __restrict__ f0in,
                                                              float4* __restrict__ f8out, float* __restrict__ f0out,
@@ -363,14 +374,14 @@ __global__ void __launch_bounds__(256, MINB) bgk_step_kernel(Stencil S, const fl
     if (p >= S.n) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
-    bgk_node<KQ, LPN>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
+    bgk_node<KQ, LPN, true, false, SPEC>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
 }
 
 // Persistent form: gridDim.x resident blocks walk the node tiles; before a
 // tile, warp 0 prefetches the stencil rows of the tile `dist` rounds ahead
 // into L2, so the streamed loads of later tiles hit L2 instead of waiting on
 // HBM while this tile gathers and collides.
-template <int KQ, int LPN, int MINB>
+template <int KQ, int LPN, int MINB, bool SPEC = false>
 __global__ void __launch_bounds__(256, MINB) bgk_step_persistent(Stencil S, const float4* __restrict__ f8in,
                                                                  const float* __restrict__ f0in,
                                                                  float4* __restrict__ f8out,
@@ -385,7 +396,7 @@ __global__ void __launch_bounds__(256, MINB) bgk_step_persistent(Stencil S, cons
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         if (threadIdx.x < 32) prefetch_tile<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
         const int p = tile * TN + threadIdx.x / LPN;
-        if (p < S.n) bgk_node<KQ, LPN>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
+        if (p < S.n) bgk_node<KQ, LPN, true, false, SPEC>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
     }
 }
 
@@ -435,16 +446,16 @@ __device__ __forceinline__ void prefetch_tile_rbf(const Stencil& S, int base, in
     }
 }
 
-template <int KQ, int MINB>
+template <int KQ, int MINB, bool SPEC = false>
 __global__ void __launch_bounds__(256, MINB) bgk_step_rbf(Stencil S, const float4* __restrict__ f8in,
                                                           const float* __restrict__ f0in, float4* __restrict__ f8out,
                                                           float* __restrict__ f0out, Collide C) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= S.n) return;
-    bgk_node<KQ, 1, true, true>(S, f8in, f0in, f8out, f0out, C, p, 0, 1u << (threadIdx.x & 31u));
+    bgk_node<KQ, 1, true, true, SPEC>(S, f8in, f0in, f8out, f0out, C, p, 0, 1u << (threadIdx.x & 31u));
 }
 
-template <int KQ, int MINB>
+template <int KQ, int MINB, bool SPEC = false>
 __global__ void __launch_bounds__(256, MINB) bgk_step_rbf_persistent(Stencil S, const float4* __restrict__ f8in,
                                                                      const float* __restrict__ f0in,
                                                                      float4* __restrict__ f8out,
@@ -457,7 +468,7 @@ __global__ void __launch_bounds__(256, MINB) bgk_step_rbf_persistent(Stencil S, 
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         if (threadIdx.x < 32) prefetch_tile_rbf<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
         const int p = tile * TN + threadIdx.x;
-        if (p < S.n) bgk_node<KQ, 1, true, true>(S, f8in, f0in, f8out, f0out, C, p, 0, 1u << lane);
+        if (p < S.n) bgk_node<KQ, 1, true, true, SPEC>(S, f8in, f0in, f8out, f0out, C, p, 0, 1u << lane);
     }
 }
 
@@ -1097,9 +1108,15 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
     const int block = 256;
     if (S.Wr) {
         // RBF-FD stencils: variants 10 and 12 map to the persistent kernel
-        // (uncapped / 2 blocks per SM), 0 to the plain uncapped kernel, the
-        // rest to the plain kernel capped for 2 blocks per SM
-        if (variant == 10) {
+        // (uncapped / 2 blocks per SM), 0 to the plain uncapped kernel, 20
+        // and 21 to the plain capped and the persistent uncapped kernel with
+        // the early index loads, the rest to the plain kernel capped for 2
+        // blocks per SM
+        if (variant == 20) {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_rbf<KQC, 2, true><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C)));
+        } else if (variant == 21) {
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_rbf_persistent<KQC, 1, true>, 256, S.n, st, [&](int g) { dev::bgk_step_rbf_persistent<KQC, 1, true><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); })));
+        } else if (variant == 10) {
             MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_rbf_persistent<KQC, 1>, 256, S.n, st, [&](int g) { dev::bgk_step_rbf_persistent<KQC, 1><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); })));
         } else if (variant == 12) {
             MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_rbf_persistent<KQC, 2>, 256, S.n, st, [&](int g) { dev::bgk_step_rbf_persistent<KQC, 2><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); })));
@@ -1138,6 +1155,8 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
             }
             break;
         }
+        case 20: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_kernel<KQC, 1, 2, true><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
+        case 21: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 1, true>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 1, true><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -1176,7 +1195,9 @@ cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* ou
         case 16:
         case 17:
         case 18:
-        case 19:  // the direction split and the link split exist for the BGK state only
+        case 19:
+        case 20:
+        case 21:  // the direction split, the link split and the early index loads exist for the BGK state only
             MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
         default: return cudaErrorInvalidValue;
     }

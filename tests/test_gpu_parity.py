@@ -48,7 +48,7 @@ def gpu_ctx(w, K, s, bb_mode, params, sigma=0.7071067811865476, use_lagrange=Tru
     return ctx
 
 
-VARIANTS = list(range(20))
+VARIANTS = list(range(22))
 
 
 # ----------------------------------------------------------------- plain MLBM
@@ -104,7 +104,7 @@ def test_bgk_steps_match_oracle_elementwise(case, variant):
         assert err < pop_tol(done), (case, done, err)
 
 
-@pytest.mark.parametrize("variant", [0, 10, 11, 12])
+@pytest.mark.parametrize("variant", [0, 10, 11, 12, 20, 21])
 @pytest.mark.parametrize("case", ["jittered", "karman_small", "karman_hybrid_small", "porous_small"])
 def test_rbf_steps_match_oracle_elementwise(case, variant):
     """RBF-FD stencils (the paper's interpolant, Sec. 2.2): the GPU step against
