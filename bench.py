@@ -225,8 +225,14 @@ def run_ours(args, rank, world, local_rank):
     sts = [st_by_s[s] for _, s in CASES]
     params = [mlbm.Params(mlbm.MODEL_BGK, tau_of(re, s), 0.0, 0.0, 0.0) for re, s in CASES]
     infos = [mlbm.stencils_info(st) for st in sts]
-    # node order and kernel variant picked together by the library's autotuner
-    order, variant, tune_ms = mlbm.autotune_order(sts, params, 10)
+    if args.variant >= 0:
+        # fixed choice (for profiler runs, where the tuner's timings are distorted)
+        order, variant, tune_ms = ORDER_NAMES.index(args.node_order), args.variant, None
+        for st in st_by_s.values():
+            mlbm.stencils_set_order(st, order)
+    else:
+        # node order and kernel variant picked together by the library's autotuner
+        order, variant, tune_ms = mlbm.autotune_order(sts, params, 10)
     ctx = mlbm.batch_init(sts, params)
     mlbm.set_kernel_variant(ctx, variant)
     stream = torch.cuda.Stream()
@@ -305,6 +311,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="fixed step kernel variant instead of the autotuner (-1: autotune)")
+    ap.add_argument("--node-order", default="hilbert", choices=ORDER_NAMES,
+                    help="node order used with --variant")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
