@@ -133,12 +133,9 @@ __device__ __forceinline__ void unbasis(const float* t, float* m) {
 // Accumulate one stencil node's contribution (centred on the node's own
 // populations oa, ob) for the 8 moving directions; U..m2 is the node's
 // column of the stored matrix.
-__device__ __forceinline__ void wls_acc(const float4* __restrict__ f8, int j, float U, float V, float W, float Wp,
-                                        float m1, float m2, const float4& oa, const float4& ob, float* acc) {
-    const float4 ra = __ldg(f8 + 2 * (size_t)j);
-    const float4 rb = __ldg(f8 + 2 * (size_t)j + 1);
-    const float a1 = ra.x - oa.x, a2 = ra.y - oa.y, a3 = ra.z - oa.z, a4 = ra.w - oa.w;
-    const float a5 = rb.x - ob.x, a6 = rb.y - ob.y, a7 = rb.z - ob.z, a8 = rb.w - ob.w;
+__device__ __forceinline__ void wls_acc_diff(float a1, float a2, float a3, float a4, float a5, float a6, float a7,
+                                             float a8, float U, float V, float W, float Wp, float m1, float m2,
+                                             float* acc) {
     const float G = m1 + m2, Hh = m1 - m2;
     acc[0] = fmaf(-m1, a1, fmaf(U, a1, acc[0]));
     acc[1] = fmaf(-m2, a2, fmaf(V, a2, acc[1]));
@@ -148,6 +145,14 @@ __device__ __forceinline__ void wls_acc(const float4* __restrict__ f8, int j, fl
     acc[5] = fmaf(Hh, a6, fmaf(Wp, a6, acc[5]));
     acc[6] = fmaf(G, a7, fmaf(W, a7, acc[6]));
     acc[7] = fmaf(-Hh, a8, fmaf(Wp, a8, acc[7]));
+}
+
+__device__ __forceinline__ void wls_acc(const float4* __restrict__ f8, int j, float U, float V, float W, float Wp,
+                                        float m1, float m2, const float4& oa, const float4& ob, float* acc) {
+    const float4 ra = __ldg(f8 + 2 * (size_t)j);
+    const float4 rb = __ldg(f8 + 2 * (size_t)j + 1);
+    wls_acc_diff(ra.x - oa.x, ra.y - oa.y, ra.z - oa.z, ra.w - oa.w, rb.x - ob.x, rb.y - ob.y, rb.z - ob.z,
+                 rb.w - ob.w, U, V, W, Wp, m1, m2, acc);
 }
 
 // RBF-FD value of population k_src of the stencil at the point whose

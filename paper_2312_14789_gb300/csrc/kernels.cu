@@ -420,13 +420,88 @@ __global__ void __launch_bounds__(256, MINB) bgk_step_nolink(Stencil S, const fl
     }
 }
 
+// Second pass of the split form: a group of 16 lanes per node with links.
+// Lane r takes the stencil members j = r, r + 16, ...: it gathers a member's
+// eight populations once and adds its share both to the departure-point
+// values (stored departure basis) and, for interpolated bounce-back, to the
+// fit of each reflected population at its link point x + (1 - 2q) s e_k
+// (unbasis of the member's matrix column, evaluated at that point), so no
+// population is gathered twice.  The group sums its partials with shuffles;
+// lane 0 applies the overrides, collides and writes.  A Lagrange-kind node
+// with links is recomputed by lane 0 alone.
 template <int KQ>
 __global__ void __launch_bounds__(128) bgk_link_nodes(Stencil S, const float4* __restrict__ f8in,
                                                       const float* __restrict__ f0in, float4* __restrict__ f8out,
-                                                      float* __restrict__ f0out, Collide C) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= S.n_link_nodes) return;
-    bgk_node<KQ, 1, true>(S, f8in, f0in, f8out, f0out, C, S.link_nodes[e], 0, 1u << (threadIdx.x & 31u));
+                                                      float* __restrict__ f0out, Collide C0) {
+    const int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 4);
+    if (e >= S.n_link_nodes) return;  // the same for the whole group
+    const unsigned lane = threadIdx.x & 31u;
+    const int r = (int)(lane & 15u);
+    const unsigned gmask = 0xffffu << (lane & 16u);
+    const int p = S.link_nodes[e];
+    const uint8_t meta = S.meta[p];
+    if ((meta & 3) != 0) {
+        if (r == 0) bgk_node<KQ, 1, true>(S, f8in, f0in, f8out, f0out, C0, p, 0, 1u << lane);
+        return;
+    }
+    const LinkRec L = S.links[S.link_slot[p]];
+    const bool interp = S.bb_mode != 0;
+    const float4 oa = __ldg(f8in + 2 * (size_t)p);
+    const float4 ob = __ldg(f8in + 2 * (size_t)p + 1);
+    const float own[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+    float acc[8], lk[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = lk[k] = 0.f;
+    for (int j = r; j < 4 * KQ; j += 16) {
+        const int q = j >> 2, c = j & 3;
+        const int id = reinterpret_cast<const int*>(S.idx + (size_t)q * S.n_pad + p)[c];
+        float t[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) t[a] = reinterpret_cast<const float*>(S.M + (size_t)(a * KQ + q) * S.n_pad + p)[c];
+        const float4 ra = __ldg(f8in + 2 * (size_t)id);
+        const float4 rb = __ldg(f8in + 2 * (size_t)id + 1);
+        const float d[8] = {ra.x - oa.x, ra.y - oa.y, ra.z - oa.z, ra.w - oa.w,
+                            rb.x - ob.x, rb.y - ob.y, rb.z - ob.z, rb.w - ob.w};
+        wls_acc_diff(d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], t[0], t[1], t[2], t[3], t[4], t[5], acc);
+        if (interp) {
+            float mm[6];
+            unbasis(t, mm);
+#pragma unroll
+            for (int k = 1; k < 9; ++k) {
+                if (!((L.mask >> k) & 1u)) continue;
+                float pb[6];
+                basis_at(k, L.t[k - 1], pb);
+                float w = 0.f;
+#pragma unroll
+                for (int a = 0; a < 6; ++a) w = fmaf(pb[a], mm[a], w);
+                lk[k - 1] = fmaf(w, d[opp_of(k) - 1], lk[k - 1]);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            acc[k] += __shfl_xor_sync(gmask, acc[k], off, 16);
+            lk[k] += __shfl_xor_sync(gmask, lk[k], off, 16);
+        }
+    }
+    if (r != 0) return;
+    float g[9];
+    g[0] = f0in[p];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+        const int kp = opp_of(k);
+        if ((L.mask >> k) & 1u)
+            g[k] = interp ? own[kp - 1] + lk[k - 1] : own[kp - 1];
+        else
+            g[k] = own[k - 1] + acc[k - 1];
+    }
+    const Collide C = collide_of(S, C0, p);
+    collide_part<1>(g, C, 0);
+    f8out[2 * (size_t)p] = make_float4(g[1], g[2], g[3], g[4]);
+    f8out[2 * (size_t)p + 1] = make_float4(g[5], g[6], g[7], g[8]);
+    f0out[p] = g[0];
 }
 
 // RBF-FD stencils: one lane per node, the per-direction weights streamed
@@ -1151,7 +1226,7 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
                 MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_nolink<KQC, 3>, 256, S.n, st, [&](int g) { dev::bgk_step_nolink<KQC, 3><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); })));
             }
             if (S.n_link_nodes > 0) {
-                MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_link_nodes<KQC><<<(S.n_link_nodes + 127) / 128, 128, 0, st>>>(S, f8in, f0in, f8out, f0out, C)));
+                MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_link_nodes<KQC><<<(S.n_link_nodes + 7) / 8, 128, 0, st>>>(S, f8in, f0in, f8out, f0out, C)));
             }
             break;
         }
