@@ -313,6 +313,16 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        0 to the plain uncapped kernel, 20 and 21 to the plain capped and the
  *        persistent uncapped kernel with the early loads, and the rest to the
  *        plain kernel capped for 2 blocks
+ *   22   least-squares BGK with staged neighbourhoods: persistent blocks of
+ *        256 threads copy the union of a 256-node tile's stencil members
+ *        (32 bytes each, listed when the context is created) into shared
+ *        memory with cp.async, one tile ahead of the tile they compute, and
+ *        gather from there through 16-bit local indices; Lagrange and
+ *        equilibrium nodes and nodes with links take the global path.
+ *        Available when every tile's union has at most 1536 members (else
+ *        mlbm_set_kernel_variant returns MLBM_E_INVALID and the autotuner
+ *        skips it); RBF-FD stencils run the plain capped kernel and tau = 1
+ *        runs variant 11 for this number
  * Variants 4 and up are available for K = 12, 16, 24 and 32.
  * The default is 12 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream

@@ -81,7 +81,7 @@ struct mlbm_ctx {
 
 namespace {
 constexpr int kGraphSteps = 16;
-constexpr int kMaxVariant = 21;  // step kernel variants 0..21 (see mlbm_set_kernel_variant)
+constexpr int kMaxVariant = 22;  // step kernel variants 0..22 (see mlbm_set_kernel_variant)
 }
 
 // Cold-cache start for timed steps: reading a zeroed buffer several times the
@@ -254,6 +254,48 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
         }
     }
     c->n_link_nodes = (int)hlinknodes.size();
+    // ---- neighbourhood staging (variant 22, least-squares BGK): per tile of
+    // kStageTile nodes the sorted union of the stencil members of its
+    // least-squares nodes without links, and each member's local index
+    std::vector<uint16_t> hlidx;
+    std::vector<int> hsoff, hsids;
+    int stage_max = 0;
+    if (p->model == MLBM_MODEL_BGK && !rbf && tma_supported(Kq)) {
+        const int64_t T = dev::kStageTile, nt = (n + T - 1) / T;
+        std::vector<std::vector<int>> lists((size_t)nt);
+        hlidx.assign((size_t)Kq * np * 4, 0);
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t b = 0; b < nt; ++b) {
+            std::vector<int>& L = lists[(size_t)b];
+            const int64_t q0 = b * T, q1 = std::min<int64_t>(n, q0 + T);
+            for (int64_t q = q0; q < q1; ++q)
+                if ((hmeta[q] & 7) == 0)
+                    for (int jj = 0; jj < K; ++jj) L.push_back(hidx[(((size_t)(jj / 4)) * np + q) * 4 + (jj % 4)]);
+            std::sort(L.begin(), L.end());
+            L.erase(std::unique(L.begin(), L.end()), L.end());
+            if ((int64_t)L.size() > dev::kStageMax) continue;  // too wide: the whole structure is dropped below
+            for (int64_t q = q0; q < q1; ++q)
+                if ((hmeta[q] & 7) == 0)
+                    for (int jj = 0; jj < K; ++jj) {
+                        const size_t at = (((size_t)(jj / 4)) * np + q) * 4 + (jj % 4);
+                        hlidx[at] = (uint16_t)(std::lower_bound(L.begin(), L.end(), hidx[at]) - L.begin());
+                    }
+        }
+        hsoff.assign((size_t)nt + 1, 0);
+        for (int64_t b = 0; b < nt; ++b) {
+            stage_max = std::max(stage_max, (int)lists[(size_t)b].size());
+            hsoff[(size_t)b + 1] = hsoff[(size_t)b] + (int)lists[(size_t)b].size();
+        }
+        if (stage_max <= dev::kStageMax && (int64_t)hsoff.back() < (int64_t)1 << 30) {
+            hsids.reserve((size_t)hsoff.back() + 8);
+            for (const auto& L : lists) hsids.insert(hsids.end(), L.begin(), L.end());
+            hsids.resize((size_t)hsoff.back() + 8, 0);  // the L2 prefetch reads whole 16-byte groups
+        } else {
+            hlidx.clear();
+            hsoff.clear();
+            stage_max = 0;
+        }
+    }
     // ---- device buffers
     MLBM_TRY(dalloc(c, &c->idx, (size_t)Kq * np));
     MLBM_TRY(dalloc(c, &c->M, (size_t)6 * Kq * np));
@@ -332,6 +374,25 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     c->S.link_nodes = c->link_nodes;
     c->S.Wr = dW;
     c->S.n_link_nodes = c->n_link_nodes;
+    c->S.lidx = nullptr;
+    c->S.stage_off = nullptr;
+    c->S.stage_ids = nullptr;
+    c->S.stage_max = 0;
+    if (!hsoff.empty()) {  // built (a context without least-squares nodes stages nothing)
+        ushort4* dl = nullptr;
+        int *doff = nullptr, *dids = nullptr;
+        MLBM_TRY(dalloc(c, &dl, (size_t)Kq * np));
+        MLBM_TRY(dalloc(c, &doff, hsoff.size()));
+        MLBM_TRY(dalloc(c, &dids, hsids.size()));
+        MLBM_TRY(upload(c, dl, hlidx.data(), hlidx.size() * 2));
+        MLBM_TRY(upload(c, doff, hsoff.data(), hsoff.size() * 4));
+        MLBM_TRY(upload(c, dids, hsids.data(), hsids.size() * 4));
+        if (stage_max > 0) MLBM_CUDA(prepare_staged_step(Kq, stage_max));
+        c->S.lidx = dl;
+        c->S.stage_off = doff;
+        c->S.stage_ids = dids;
+        c->S.stage_max = stage_max;
+    }
     set_collide(c);
     // ---- initial state
     std::vector<double> ru((size_t)n * 3);
@@ -705,6 +766,8 @@ mlbm_status mlbm_set_kernel_variant(mlbm_ctx* c, int variant) {
     if (!c) return set_error(MLBM_E_INVALID, "set_kernel_variant: NULL context");
     if (variant < 0 || variant > kMaxVariant || (variant >= 4 && !tma_supported(c->K / 4)))
         return set_error(MLBM_E_INVALID, "set_kernel_variant: variant not available for this K");
+    if (variant == 22 && c->params.model == MLBM_MODEL_BGK && !c->S.Wr && !c->S.lidx)
+        return set_error(MLBM_E_INVALID, "set_kernel_variant: no staged neighbourhoods for this context");
     c->variant = variant;
     return MLBM_OK;
 }

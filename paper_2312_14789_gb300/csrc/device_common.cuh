@@ -55,7 +55,20 @@ struct Stencil {
     // RBF-FD stencils: per-direction weights [8 K/4][n_pad] float4 (row
     // r = direction k - 1), null for the least-squares fit
     const float4* Wr;
+    // neighbourhood staging (step variant 22, least-squares BGK): for each
+    // tile of kStageTile consecutive nodes the sorted union of the stencil
+    // members of its least-squares nodes without links (stage_ids, from
+    // stage_off[tile] to stage_off[tile + 1]), at most stage_max per tile,
+    // and each member's position in its tile's list as a 16-bit local index
+    // [K/4][n_pad] ushort4 (slot order as idx); all null when not built
+    const ushort4* lidx;
+    const int* stage_off;
+    const int* stage_ids;
+    int stage_max;
 };
+
+constexpr int kStageTile = 256;   // nodes per staged tile (one block)
+constexpr int kStageMax = 1536;   // largest neighbourhood that is staged (48 KiB per buffer)
 
 // collision parameters of node p
 __device__ __forceinline__ Collide collide_of(const Stencil& S, const Collide& C0, int p) {

@@ -504,6 +504,124 @@ __global__ void __launch_bounds__(128) bgk_link_nodes(Stencil S, const float4* _
     f0out[p] = g[0];
 }
 
+// ---------------------------------------------- staged neighbourhoods (22)
+// Persistent blocks walk the node tiles.  A tile's neighbourhood (the sorted
+// union of its least-squares nodes' stencil members, listed on the host) is
+// copied into shared memory by cp.async, 32 bytes per member, one tile ahead
+// of the tile being computed (two buffers); the nodes then gather from shared
+// memory through 16-bit local indices, which also halves the index bytes.
+// Nodes of other kinds and nodes with bounce-back links take the global path.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int KQ>
+__device__ __forceinline__ void prefetch_tile_staged(const Stencil& S, int tile, int n_tiles, unsigned lane) {
+    if (tile >= n_tiles) return;
+    const int base = tile * kStageTile;
+    const int nodes = min(kStageTile, S.n_pad - base);
+    for (int c = (int)lane; c < 7 * KQ + 2; c += 32) {
+        if (c < 6 * KQ)
+            prefetch_l2(S.M + (size_t)c * S.n_pad + base, (uint32_t)nodes * 16u);
+        else if (c < 7 * KQ)
+            prefetch_l2(S.lidx + (size_t)(c - 6 * KQ) * S.n_pad + base, (uint32_t)nodes * 8u);
+        else if (c == 7 * KQ)
+            prefetch_l2(S.meta + base, (uint32_t)((nodes + 15) / 16 * 16));
+        else {
+            // the member list, widened to 16-byte bounds (the list is padded)
+            const int a0 = __ldg(S.stage_off + tile) & ~3, a1 = (__ldg(S.stage_off + tile + 1) + 3) & ~3;
+            if (a1 > a0) prefetch_l2(S.stage_ids + a0, (uint32_t)(a1 - a0) * 4u);
+        }
+    }
+}
+
+__device__ __forceinline__ void stage_tile(const Stencil& S, const float4* __restrict__ f8in, float4* buf, int tile,
+                                           int n_tiles) {
+    if (tile < n_tiles) {
+        const int a0 = __ldg(S.stage_off + tile), a1 = __ldg(S.stage_off + tile + 1);
+        for (int i = a0 + (int)threadIdx.x; i < a1; i += (int)blockDim.x) {
+            const int id = __ldg(S.stage_ids + i);
+            cp_async16(buf + 2 * (i - a0), f8in + 2 * (size_t)id);
+            cp_async16(buf + 2 * (i - a0) + 1, f8in + 2 * (size_t)id + 1);
+        }
+    }
+    cp_async_commit();  // an empty group past the last tile keeps the wait counts uniform
+}
+
+template <int KQ>
+__device__ __forceinline__ void staged_node(const Stencil& S, const float4* nb, const float4* __restrict__ f8in,
+                                            const float* __restrict__ f0in, float4* __restrict__ f8out,
+                                            float* __restrict__ f0out, const Collide& C0, int p) {
+    const uint8_t meta = S.meta[p];
+    if ((meta & 7) != 0) {
+        bgk_node<KQ, 1, true>(S, f8in, f0in, f8out, f0out, C0, p, 0, 1u << (threadIdx.x & 31u));
+        return;
+    }
+    const Collide C = collide_of(S, C0, p);
+    const float4 oa = __ldg(f8in + 2 * (size_t)p);
+    const float4 ob = __ldg(f8in + 2 * (size_t)p + 1);
+    ushort4 lv[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) lv[q] = __ldcs(S.lidx + (size_t)q * S.n_pad + p);
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        float4 m[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) m[a] = ld_stream(S.M + (size_t)(a * KQ + q) * S.n_pad + p);
+        const float* mc = reinterpret_cast<const float*>(m);
+        const int l[4] = {lv[q].x, lv[q].y, lv[q].z, lv[q].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float4 ra = nb[2 * l[c]];
+            const float4 rb = nb[2 * l[c] + 1];
+            wls_acc_diff(ra.x - oa.x, ra.y - oa.y, ra.z - oa.z, ra.w - oa.w, rb.x - ob.x, rb.y - ob.y, rb.z - ob.z,
+                         rb.w - ob.w, mc[c], mc[4 + c], mc[8 + c], mc[12 + c], mc[16 + c], mc[20 + c], acc);
+        }
+    }
+    const float own[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+    float g[9];
+    g[0] = f0in[p];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) g[k] = acc[k - 1] + own[k - 1];
+    collide_part<1>(g, C, 0);
+    f8out[2 * (size_t)p] = make_float4(g[1], g[2], g[3], g[4]);
+    f0out[p] = g[0];
+    f8out[2 * (size_t)p + 1] = make_float4(g[5], g[6], g[7], g[8]);
+}
+
+template <int KQ>
+__global__ void __launch_bounds__(256, 2) bgk_step_staged(Stencil S, const float4* __restrict__ f8in,
+                                                          const float* __restrict__ f0in, float4* __restrict__ f8out,
+                                                          float* __restrict__ f0out, Collide C) {
+    extern __shared__ float4 nbuf[];  // two buffers of 2 * stage_max float4
+    const int n_tiles = (S.n + kStageTile - 1) / kStageTile;
+    const unsigned lane = threadIdx.x & 31u;
+    float4* const buf0 = nbuf;
+    float4* const buf1 = nbuf + 2 * (size_t)S.stage_max;
+    if (threadIdx.x < 32) prefetch_tile_staged<KQ>(S, blockIdx.x, n_tiles, lane);
+    stage_tile(S, f8in, buf0, blockIdx.x, n_tiles);
+    int it = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+        if (threadIdx.x < 32) prefetch_tile_staged<KQ>(S, tile + gridDim.x, n_tiles, lane);
+        stage_tile(S, f8in, (it & 1) ? buf0 : buf1, tile + gridDim.x, n_tiles);
+        cp_async_wait<1>();  // this thread's copies of the current tile have landed
+        __syncthreads();     // and every thread's
+        const int p = tile * kStageTile + threadIdx.x;
+        if (p < S.n) staged_node<KQ>(S, (it & 1) ? buf1 : buf0, f8in, f0in, f8out, f0out, C, p);
+        __syncthreads();  // the buffer is free for the tile after next
+    }
+    cp_async_wait<0>();
+}
+
 // RBF-FD stencils: one lane per node, the per-direction weights streamed
 // instead of the least-squares matrix; plain grid or persistent blocks that
 // prefetch later tiles' weight, index and meta rows into L2.
@@ -1162,16 +1280,23 @@ inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 // grid of exactly the resident blocks (occupancy API), at most one per tile
 template <class F>
-cudaError_t run_persistent(const void* fn, int tile_nodes, int n, cudaStream_t, F launch) {
+cudaError_t run_persistent(const void* fn, int tile_nodes, int n, cudaStream_t, F launch, size_t smem = 0) {
     int dev_id = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev_id);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
     if (e != cudaSuccess) return e;
     const int tiles = (n + tile_nodes - 1) / tile_nodes;
     const int grid = std::max(1, std::min(tiles, sms * std::max(per_sm, 1)));
     launch(grid);
     return cudaSuccess;
+}
+
+// allow the staged kernel the dynamic shared memory of its two buffers
+cudaError_t prepare_staged_step(int Kq, int stage_max) {
+    const int smem = 4 * stage_max * (int)sizeof(float4);
+    MLBM_DISPATCH_KQ_MAIN(Kq, (cudaFuncSetAttribute((const void*)dev::bgk_step_staged<KQC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)));
+    return cudaGetLastError();
 }
 
 // variant v: lanes per node and minimum resident blocks (register cap)
@@ -1230,6 +1355,12 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
             }
             break;
         }
+        case 22: {
+            if (!S.lidx) return cudaErrorInvalidValue;  // no staging structure for this context
+            const size_t smem = (size_t)4 * S.stage_max * sizeof(float4);
+            MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_staged<KQC>, dev::kStageTile, S.n, st, [&](int g) { dev::bgk_step_staged<KQC><<<g, block, smem, st>>>(S, f8in, f0in, f8out, f0out, C); }, smem)));
+            break;
+        }
         case 20: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_kernel<KQC, 1, 2, true><<<blocks_for(S.n, block), block, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         case 21: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 1, true>, 256, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 1, true><<<g, block, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }))); break;
         default: return cudaErrorInvalidValue;
@@ -1272,7 +1403,8 @@ cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* ou
         case 18:
         case 19:
         case 20:
-        case 21:  // the direction split, the link split and the early index loads exist for the BGK state only
+        case 21:
+        case 22:  // the direction split, the link split, the early index loads and the staging exist for the BGK state only
             MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
         default: return cudaErrorInvalidValue;
     }

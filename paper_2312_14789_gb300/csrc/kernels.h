@@ -11,6 +11,8 @@ namespace mlbm {
 
 cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,
                             float* f0out, const dev::Collide& C, int variant, cudaStream_t st);
+// raises the dynamic shared-memory limit of the staged step kernel (variant 22)
+cudaError_t prepare_staged_step(int Kq, int stage_max);
 cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C, int variant,
                              cudaStream_t st);
 cudaError_t launch_set_bgk(int n, const int* perm, const double* f, float4* f8, float* f0, cudaStream_t st);
