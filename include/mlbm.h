@@ -323,6 +323,10 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        mlbm_set_kernel_variant returns MLBM_E_INVALID and the autotuner
  *        skips it); RBF-FD stencils run the plain capped kernel and tau = 1
  *        runs variant 11 for this number
+ *   23-24 other block sizes with the register budget of 12 and 11: 23 = as 12
+ *        with blocks of 128 threads (128-node tiles, capped for 4 resident
+ *        blocks); 24 = as 11 with blocks of 512 threads (BGK only; RBF-FD
+ *        stencils run the plain capped kernel, tau = 1 runs variant 11)
  * Variants 4 and up are available for K = 12, 16, 24 and 32.
  * The default is 12 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream

@@ -81,7 +81,7 @@ struct mlbm_ctx {
 
 namespace {
 constexpr int kGraphSteps = 16;
-constexpr int kMaxVariant = 22;  // step kernel variants 0..22 (see mlbm_set_kernel_variant)
+constexpr int kMaxVariant = 24;  // step kernel variants 0..24 (see mlbm_set_kernel_variant)
 }
 
 // Cold-cache start for timed steps: reading a zeroed buffer several times the

@@ -363,8 +363,8 @@ __device__ __forceinline__ void prefetch_tile(const Stencil& S, int base, int tn
     }
 }
 
-template <int KQ, int LPN, int MINB, bool SPEC = false>
-__global__ void __launch_bounds__(256, MINB) bgk_step_kernel(Stencil S, const float4* __restrict__ f8in,
+template <int KQ, int LPN, int MINB, bool SPEC = false, int BS = 256>
+__global__ void __launch_bounds__(BS, MINB) bgk_step_kernel(Stencil S, const float4* __restrict__ f8in,
                                                              const float* __restrict__ f0in,
                                                              float4* __restrict__ f8out, float* __restrict__ f0out,
                                                              Collide C) {
@@ -381,12 +381,12 @@ __global__ void __launch_bounds__(256, MINB) bgk_step_kernel(Stencil S, const fl
 // tile, warp 0 prefetches the stencil rows of the tile `dist` rounds ahead
 // into L2, so the streamed loads of later tiles hit L2 instead of waiting on
 // HBM while this tile gathers and collides.
-template <int KQ, int LPN, int MINB, bool SPEC = false>
-__global__ void __launch_bounds__(256, MINB) bgk_step_persistent(Stencil S, const float4* __restrict__ f8in,
-                                                                 const float* __restrict__ f0in,
-                                                                 float4* __restrict__ f8out,
-                                                                 float* __restrict__ f0out, Collide C, int dist) {
-    constexpr int TN = 256 / LPN;
+template <int KQ, int LPN, int MINB, bool SPEC = false, int BS = 256>
+__global__ void __launch_bounds__(BS, MINB) bgk_step_persistent(Stencil S, const float4* __restrict__ f8in,
+                                                                const float* __restrict__ f0in,
+                                                                float4* __restrict__ f8out,
+                                                                float* __restrict__ f0out, Collide C, int dist) {
+    constexpr int TN = BS / LPN;
     const int n_tiles = (S.n + TN - 1) / TN;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
@@ -1280,11 +1280,12 @@ inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 // grid of exactly the resident blocks (occupancy API), at most one per tile
 template <class F>
-cudaError_t run_persistent(const void* fn, int tile_nodes, int n, cudaStream_t, F launch, size_t smem = 0) {
+cudaError_t run_persistent(const void* fn, int tile_nodes, int n, cudaStream_t, F launch, size_t smem = 0,
+                           int threads = 256) {
     int dev_id = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev_id);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
     if (e != cudaSuccess) return e;
     const int tiles = (n + tile_nodes - 1) / tile_nodes;
     const int grid = std::max(1, std::min(tiles, sms * std::max(per_sm, 1)));
@@ -1355,6 +1356,8 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
             }
             break;
         }
+        case 23: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 4, false, 128>, 128, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 4, false, 128><<<g, 128, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }, 0, 128))); break;
+        case 24: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_kernel<KQC, 1, 1, false, 512><<<blocks_for(S.n, 512), 512, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         case 22: {
             if (!S.lidx) return cudaErrorInvalidValue;  // no staging structure for this context
             const size_t smem = (size_t)4 * S.stage_max * sizeof(float4);
@@ -1404,7 +1407,9 @@ cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* ou
         case 19:
         case 20:
         case 21:
-        case 22:  // the direction split, the link split, the early index loads and the staging exist for the BGK state only
+        case 22:
+        case 23:
+        case 24:  // the direction split, the link split, the early index loads, the staging and the other block sizes exist for the BGK state only
             MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
         default: return cudaErrorInvalidValue;
     }

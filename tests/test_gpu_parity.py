@@ -48,7 +48,7 @@ def gpu_ctx(w, K, s, bb_mode, params, sigma=0.7071067811865476, use_lagrange=Tru
     return ctx
 
 
-VARIANTS = list(range(23))
+VARIANTS = list(range(25))
 
 
 # ----------------------------------------------------------------- plain MLBM
