@@ -28,21 +28,28 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--n-target", type=int, default=1_000_000)
     ap.add_argument("--variant", type=int, default=-1, help="kernel variant (-1: autotune)")
+    ap.add_argument("--node-order", default="hilbert", choices=["hilbert", "morton", "rows", "input"],
+                    help="device node order of the stencils")
     args = ap.parse_args()
+    order = ["hilbert", "morton", "rows", "input"].index(args.node_order)
     if args.workload == "karman_sweep":
         import bench
         w = I.karman(seed=2)
         st_by_s = {s: mlbm.build_stencils_for(w, K=16, s=s, bb_mode=mlbm.BB_SIMPLE)
                    for s in sorted({s for _, s in bench.CASES})}
+        for st in st_by_s.values():
+            mlbm.stencils_set_order(st, order)
         ctx = mlbm.batch_init([st_by_s[s] for _, s in bench.CASES],
                               [mlbm.Params(mlbm.MODEL_BGK, bench.tau_of(re, s), 0.0, 0.0, 0.0) for re, s in bench.CASES])
     elif args.workload == "karman":
         w = I.karman(seed=2)
         st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=mlbm.BB_SIMPLE)
+        mlbm.stencils_set_order(st, order)
         ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, 0.62, 0.0, 0.0, 0.0))
     else:
         w = I.porous(seed=3, n_target=args.n_target)
         st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=mlbm.BB_INTERPOLATED)
+        mlbm.stencils_set_order(st, order)
         ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, 1e-6, 0.0))
     if args.variant >= 0:
         mlbm.set_kernel_variant(ctx, args.variant)
