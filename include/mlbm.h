@@ -327,6 +327,11 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        with blocks of 128 threads (128-node tiles, capped for 4 resident
  *        blocks); 24 = as 11 with blocks of 512 threads (BGK only; RBF-FD
  *        stencils run the plain capped kernel, tau = 1 runs variant 11)
+ *   25-26 as 12 (persistent) and 11 (plain grid), launched with programmatic
+ *        stream serialization: each step grid lets the next one be scheduled
+ *        on the SM slots it frees, and the next grid prefetches its first
+ *        stencil rows into L2 before it waits for the previous grid's writes
+ *        (BGK and tau = 1; RBF-FD stencils run the plain capped kernel)
  * Variants 4 and up are available for K = 12, 16, 24 and 32.
  * The default is 12 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream

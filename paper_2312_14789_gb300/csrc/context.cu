@@ -81,7 +81,7 @@ struct mlbm_ctx {
 
 namespace {
 constexpr int kGraphSteps = 16;
-constexpr int kMaxVariant = 24;  // step kernel variants 0..24 (see mlbm_set_kernel_variant)
+constexpr int kMaxVariant = 26;  // step kernel variants 0..26 (see mlbm_set_kernel_variant)
 }
 
 // Cold-cache start for timed steps: reading a zeroed buffer several times the
@@ -823,7 +823,7 @@ mlbm_status mlbm_autotune_ex(mlbm_ctx* c, int steps_per_variant, int flush_l2, d
     int best = c->variant;
     double best_t = 1e30;
     for (int v = 0; v <= kMaxVariant && st == MLBM_OK; ++v) {
-        if (v >= 14 && c->params.model != MLBM_MODEL_BGK) continue;
+        if (v >= 14 && v <= 24 && c->params.model != MLBM_MODEL_BGK) continue;
         if (v >= 4 && !tma_supported(c->K / 4)) continue;
         // one untimed warm-up launch, then the timed ones
         st = launch_one_step(c, v);

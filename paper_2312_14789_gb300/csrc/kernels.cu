@@ -363,11 +363,25 @@ __device__ __forceinline__ void prefetch_tile(const Stencil& S, int base, int tn
     }
 }
 
-template <int KQ, int LPN, int MINB, bool SPEC = false, int BS = 256>
+// Programmatic dependent launch (variants 25, 26): a step grid lets the next
+// step's grid be scheduled on the SM slots it frees (launch_dependents), and
+// the next grid issues only reads of the fixed stencil rows (L2 prefetch)
+// before it waits for the previous grid to complete and its writes to be
+// visible (wait); populations are read and written only after the wait.
+// Without a programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <int KQ, int LPN, int MINB, bool SPEC = false, int BS = 256, bool PDL = false>
 __global__ void __launch_bounds__(BS, MINB) bgk_step_kernel(Stencil S, const float4* __restrict__ f8in,
                                                              const float* __restrict__ f0in,
                                                              float4* __restrict__ f8out, float* __restrict__ f0out,
                                                              Collide C) {
+    if (PDL) {
+        if (threadIdx.x < 32) prefetch_tile<KQ>(S, blockIdx.x * (BS / LPN), BS / LPN, threadIdx.x & 31u);
+        pdl_trigger();
+        pdl_wait();
+    }
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = tid / LPN;
     const int h = tid % LPN;
@@ -381,7 +395,7 @@ __global__ void __launch_bounds__(BS, MINB) bgk_step_kernel(Stencil S, const flo
 // tile, warp 0 prefetches the stencil rows of the tile `dist` rounds ahead
 // into L2, so the streamed loads of later tiles hit L2 instead of waiting on
 // HBM while this tile gathers and collides.
-template <int KQ, int LPN, int MINB, bool SPEC = false, int BS = 256>
+template <int KQ, int LPN, int MINB, bool SPEC = false, int BS = 256, bool PDL = false>
 __global__ void __launch_bounds__(BS, MINB) bgk_step_persistent(Stencil S, const float4* __restrict__ f8in,
                                                                 const float* __restrict__ f0in,
                                                                 float4* __restrict__ f8out,
@@ -393,6 +407,10 @@ __global__ void __launch_bounds__(BS, MINB) bgk_step_persistent(Stencil S, const
     const int h = threadIdx.x % LPN;
     if (threadIdx.x < 32)
         for (int d = 0; d < dist; ++d) prefetch_tile<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    if (PDL) {
+        pdl_trigger();
+        pdl_wait();
+    }
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         if (threadIdx.x < 32) prefetch_tile<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
         const int p = tile * TN + threadIdx.x / LPN;
@@ -857,9 +875,14 @@ __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __rest
     }
 }
 
-template <int KQ, int LPN, int MINB>
+template <int KQ, int LPN, int MINB, bool PDL = false>
 __global__ void __launch_bounds__(256, MINB) tau1_step_kernel(Stencil S, const float4* __restrict__ in,
                                                               float4* __restrict__ out, Collide C) {
+    if (PDL) {
+        if (threadIdx.x < 32) prefetch_tile<KQ>(S, blockIdx.x * (256 / LPN), 256 / LPN, threadIdx.x & 31u);
+        pdl_trigger();
+        pdl_wait();
+    }
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = tid / LPN;
     const int h = tid % LPN;
@@ -892,7 +915,7 @@ __global__ void __launch_bounds__(256, MINB) tau1_step_rbf_persistent(Stencil S,
     }
 }
 
-template <int KQ, int LPN, int MINB>
+template <int KQ, int LPN, int MINB, bool PDL = false>
 __global__ void __launch_bounds__(256, MINB) tau1_step_persistent(Stencil S, const float4* __restrict__ in,
                                                                   float4* __restrict__ out, Collide C, int dist) {
     constexpr int TN = 256 / LPN;
@@ -902,6 +925,10 @@ __global__ void __launch_bounds__(256, MINB) tau1_step_persistent(Stencil S, con
     const int h = threadIdx.x % LPN;
     if (threadIdx.x < 32)
         for (int d = 0; d < dist; ++d) prefetch_tile<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    if (PDL) {
+        pdl_trigger();
+        pdl_wait();
+    }
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         if (threadIdx.x < 32) prefetch_tile<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
         const int p = tile * TN + threadIdx.x / LPN;
@@ -1293,6 +1320,23 @@ cudaError_t run_persistent(const void* fn, int tile_nodes, int n, cudaStream_t, 
     return cudaSuccess;
 }
 
+// launch with programmatic stream serialization (the kernel waits for its
+// predecessor itself, see pdl_wait)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // allow the staged kernel the dynamic shared memory of its two buffers
 cudaError_t prepare_staged_step(int Kq, int stage_max) {
     const int smem = 4 * stage_max * (int)sizeof(float4);
@@ -1356,6 +1400,8 @@ cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const flo
             }
             break;
         }
+        case 25: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 2, false, 256, true>, 256, S.n, st, [&](int g) { (void)launch_pdl(dev::bgk_step_persistent<KQC, 1, 2, false, 256, true>, g, block, st, S, f8in, f0in, f8out, f0out, C, 1); }))); break;
+        case 26: MLBM_DISPATCH_KQ_MAIN(S.Kq, ((void)launch_pdl(dev::bgk_step_kernel<KQC, 1, 2, false, 256, true>, blocks_for(S.n, block), block, st, S, f8in, f0in, f8out, f0out, C))); break;
         case 23: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::bgk_step_persistent<KQC, 1, 4, false, 128>, 128, S.n, st, [&](int g) { dev::bgk_step_persistent<KQC, 1, 4, false, 128><<<g, 128, 0, st>>>(S, f8in, f0in, f8out, f0out, C, 1); }, 0, 128))); break;
         case 24: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::bgk_step_kernel<KQC, 1, 1, false, 512><<<blocks_for(S.n, 512), 512, 0, st>>>(S, f8in, f0in, f8out, f0out, C))); break;
         case 22: {
@@ -1399,6 +1445,8 @@ cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* ou
         case 11: MLBM_DISPATCH_KQ_MAIN(S.Kq, (dev::tau1_step_kernel<KQC, 1, 2><<<blocks_for(S.n, block), block, 0, st>>>(S, in, out, C))); break;
         case 12: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 2>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 2><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
         case 13: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 3>, 256, S.n, st, [&](int g) { dev::tau1_step_persistent<KQC, 1, 3><<<g, block, 0, st>>>(S, in, out, C, 1); }))); break;
+        case 25: MLBM_DISPATCH_KQ_MAIN(S.Kq, (run_persistent((const void*)dev::tau1_step_persistent<KQC, 1, 2, true>, 256, S.n, st, [&](int g) { (void)launch_pdl(dev::tau1_step_persistent<KQC, 1, 2, true>, g, block, st, S, in, out, C, 1); }))); break;
+        case 26: MLBM_DISPATCH_KQ_MAIN(S.Kq, ((void)launch_pdl(dev::tau1_step_kernel<KQC, 1, 2, true>, blocks_for(S.n, block), block, st, S, in, out, C))); break;
         case 14:
         case 15:
         case 16:
