@@ -333,7 +333,7 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        stencil rows into L2 before it waits for the previous grid's writes
  *        (BGK and tau = 1; RBF-FD stencils run the plain capped kernel)
  * Variants 4 and up are available for K = 12, 16, 24 and 32.
- * The default is 12 when available, else 1.  mlbm_autotune times every
+ * The default is 25 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream
  * (state saved and restored, step count unchanged), keeps the fastest and
  * returns its per-step time in *best_ms (may be NULL).

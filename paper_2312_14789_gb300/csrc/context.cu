@@ -61,7 +61,7 @@ struct mlbm_ctx {
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = -1.0;
-    int variant = 12;
+    int variant = 25;
     int* err = nullptr;  // device error word of the bounded waits
     dev::Stencil S{};
     dev::Collide C{};
