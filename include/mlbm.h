@@ -224,6 +224,24 @@ mlbm_status mlbm_step(mlbm_ctx* ctx, int64_t n_steps);
 int64_t mlbm_step_count(const mlbm_ctx* ctx);
 
 /*
+ * Force of the fluid on the walls by integrating the fluid stress along the
+ * given wall nodes (an alternative to the momentum exchange of mlbm_drag_lift;
+ * the paper does not say how it evaluates the force of Sec. 3.1).  For each
+ * listed node i (caller's order id nodes[i], a least-squares node on a wall):
+ * traction sigma n_i ds_i / s with sigma = -(rho - 1)/3 I + rho nu (grad u +
+ * grad u^T), nu = (tau - 1/2)/3, grad u from the node's own least-squares fit
+ * (lattice units of the streaming distance s), n_i = normals[i][2] the unit
+ * normal pointing out of the solid into the fluid, ds_i = ds[i] the wall
+ * length the node stands for (node-spacing units).  F = sum of the tractions
+ * (FP64, summed in list order) in the units of mlbm_drag_lift.  Single-sample
+ * least-squares contexts only (else MLBM_E_INVALID); a listed node that is not
+ * a least-squares node, or an id out of range, gives MLBM_E_INVALID.  Arrays
+ * are caller-owned host memory, read during the call; m = 0 gives F = 0.
+ */
+mlbm_status mlbm_wall_stress_force(mlbm_ctx* ctx, const int64_t* nodes, const double* normals, const double* ds,
+                                   int64_t m, double* fx, double* fy);
+
+/*
  * Density and velocity of the current state at every node (caller's order):
  * rho[n], u[n][2].  For BGK these are the moments the last collision used
  * (rho = sum f, rho u = sum f e - rho g / 2).  Either pointer may be NULL.

@@ -332,6 +332,38 @@ def force_mlbm1(op: Operator, ru, g=(0.0, 0.0)):
     return float(fx[0]), float(fy[0])
 
 
+def wall_stress_force(op: Operator, ru, tau, nodes, normals, ds):
+    """Force of the fluid on the walls by integrating the fluid stress along
+    them (a reading: the paper is silent on how it evaluates the force of
+    Sec. 3.1).  At each wall node i, with outward-from-solid unit normal n and
+    wall length ds (node-spacing units), the traction is
+        sigma n,  sigma = -(rho - 1)/3 I + rho nu (grad u + grad u^T),
+    nu = (tau - 1/2)/3 (Eq. (6)), in lattice units of the streaming distance s;
+    grad u comes from the node's own least-squares fit (rows 1 and 2 of its
+    matrix M, which already carry the factor s of the lattice unit), and
+    F = sum_i sigma_i n_i ds_i / s.  ru[n][3] = (rho, ux, uy) in the caller's
+    order; the nodes must be least-squares nodes of `op`."""
+    assert op.targets is None
+    ru = np.asarray(ru, np.float64)
+    nu = (float(tau) - 0.5) / 3.0
+    F = np.zeros(2)
+    for i, n, l in zip(np.asarray(nodes, np.int64), np.asarray(normals, np.float64), np.asarray(ds, np.float64)):
+        if op.kind[i] != 0:
+            raise ValueError(f"node {i} is not a least-squares node")
+        j = op.idx[i]
+        du = ru[j, 1] - ru[i, 1]
+        dv = ru[j, 2] - ru[i, 2]
+        ux_x, ux_y = op.M[i, 1] @ du, op.M[i, 2] @ du
+        uy_x, uy_y = op.M[i, 1] @ dv, op.M[i, 2] @ dv
+        rho = ru[i, 0]
+        p = (rho - 1.0) / 3.0
+        sxx = -p + 2.0 * rho * nu * ux_x
+        syy = -p + 2.0 * rho * nu * uy_y
+        sxy = rho * nu * (ux_y + uy_x)
+        F += np.array([sxx * n[0] + sxy * n[1], sxy * n[0] + syy * n[1]]) * l / op.s
+    return float(F[0]), float(F[1])
+
+
 # --------------------------------------------------------------------------
 # observables (Sec. 3.2, Eq. (23) and (25); Sec. 3.1 Strouhal number)
 # --------------------------------------------------------------------------

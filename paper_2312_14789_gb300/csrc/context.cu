@@ -664,6 +664,62 @@ mlbm_status mlbm_macroscopics(mlbm_ctx* c, double* rho, double* u) {
     return MLBM_OK;
 }
 
+mlbm_status mlbm_wall_stress_force(mlbm_ctx* c, const int64_t* nodes, const double* normals, const double* ds,
+                                   int64_t m, double* fx, double* fy) {
+    if (!c || (m > 0 && (!nodes || !normals || !ds)) || m < 0)
+        return set_error(MLBM_E_INVALID, "wall_stress_force: bad arguments");
+    if (c->seg_off.size() > 2) return set_error(MLBM_E_INVALID, "wall_stress_force: single-sample contexts only");
+    if (c->S.Wr) return set_error(MLBM_E_INVALID, "wall_stress_force: least-squares stencils only");
+    if (m > (int64_t)1 << 30) return set_error(MLBM_E_INVALID, "wall_stress_force: too many wall nodes");
+    // caller's node ids -> device positions
+    std::vector<int> perm((size_t)c->n_pad), pos((size_t)m);
+    MLBM_CUDA(cudaMemcpyAsync(perm.data(), c->perm, (size_t)c->n_pad * 4, cudaMemcpyDeviceToHost, c->stream));
+    MLBM_TRY(sync(c));
+    std::vector<int> inv((size_t)c->n, -1);
+    for (int64_t q = 0; q < c->n; ++q) inv[(size_t)perm[(size_t)q]] = (int)q;
+    for (int64_t i = 0; i < m; ++i) {
+        if (nodes[i] < 0 || nodes[i] >= c->n) return set_error(MLBM_E_INVALID, "wall_stress_force: node id out of range");
+        pos[(size_t)i] = inv[(size_t)nodes[i]];
+    }
+    double sx = 0.0, sy = 0.0;
+    if (m > 0) {
+        int* dpos = nullptr;
+        double *dn = nullptr, *dds = nullptr, *dout = nullptr;
+        const size_t mm = (size_t)m;
+        cudaError_t e = cudaMalloc(&dpos, mm * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&dn, mm * 16);
+        if (e == cudaSuccess) e = cudaMalloc(&dds, mm * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&dout, mm * 16);
+        std::vector<double> out(2 * mm, 0.0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpos, pos.data(), mm * 4, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dn, normals, mm * 16, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dds, ds, mm * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) {
+            const int model = c->params.model == MLBM_MODEL_BGK ? 0 : 1;
+            const double nu = (c->params.tau - 0.5) / 3.0;
+            e = launch_wall_traction(c->S, model, c->f8[c->cur], c->f0[c->cur], c->ruv[c->cur], c->C.ax, c->C.ay,
+                                     nu, c->s, dpos, dn, dds, (int)m, dout, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), dout, mm * 16, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(dpos);
+        cudaFree(dn);
+        cudaFree(dds);
+        cudaFree(dout);
+        if (e != cudaSuccess) return set_error(MLBM_E_CUDA, std::string("wall_stress_force: ") + cudaGetErrorString(e));
+        for (size_t i = 0; i < mm; ++i) {  // fixed order: reproducible
+            if (std::isnan(out[2 * i])) return set_error(MLBM_E_INVALID, "wall_stress_force: node " +
+                                                                         std::to_string(nodes[i]) +
+                                                                         " is not a least-squares node");
+            sx += out[2 * i];
+            sy += out[2 * i + 1];
+        }
+    }
+    if (fx) *fx = sx;
+    if (fy) *fy = sy;
+    return MLBM_OK;
+}
+
 mlbm_status mlbm_drag_lift(mlbm_ctx* c, double ref_length, double u_ref, double* fx, double* fy, double* cd,
                            double* cl) {
     if (!c) return set_error(MLBM_E_INVALID, "drag_lift: NULL context");

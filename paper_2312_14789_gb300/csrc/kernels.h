@@ -11,6 +11,11 @@ namespace mlbm {
 
 cudaError_t launch_bgk_step(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,
                             float* f0out, const dev::Collide& C, int variant, cudaStream_t st);
+// wall tractions of the listed wall nodes (device positions pos[m], normals
+// nrm[m][2], wall lengths ds[m]) into out[m][2], FP64 (wall_stress.cu)
+cudaError_t launch_wall_traction(const dev::Stencil& S, int model, const float4* f8, const float* f0,
+                                 const float4* ruv, float ax, float ay, double nu, double s, const int* pos,
+                                 const double* nrm, const double* ds, int m, double* out, cudaStream_t st);
 // raises the dynamic shared-memory limit of the staged step kernel (variant 22)
 cudaError_t prepare_staged_step(int Kq, int stage_max);
 cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C, int variant,

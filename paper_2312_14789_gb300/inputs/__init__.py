@@ -462,6 +462,67 @@ def cylinder_array(side: float = 40.0, radius: float = 8.0, h: float = 1.0, seed
                     {"seed": seed, "solid_fraction": float(np.pi * radius ** 2 / side ** 2), "L": side})
 
 
+def wall_geometry(w: Workload, tol: float = 1e-6):
+    """Wall nodes on the solid disks and on the straight solid sides of a node
+    set, with the unit normal pointing out of the solid into the fluid and the
+    length of wall each node stands for (half the gaps to its two neighbours
+    along the same surface).  Returns (nodes int64[m], normals[m][2], ds[m]).
+    Geometry only: used to integrate a wall traction along the surfaces."""
+    x0, y0, x1, y1 = w.box
+    lx, ly = x1 - x0, y1 - y0
+    per_x, per_y = w.sides[0] == PERIODIC, w.sides[2] == PERIODIC
+    wall = np.nonzero(w.node_class == WALL)[0]
+    nodes, nrm, ds = [], [], []
+    for (cx, cy, r) in np.asarray(w.disks, np.float64).reshape(-1, 3):
+        d = w.xy[wall] - np.array([cx, cy])
+        if per_x:
+            d[:, 0] -= lx * np.round(d[:, 0] / lx)
+        if per_y:
+            d[:, 1] -= ly * np.round(d[:, 1] / ly)
+        on = np.abs(np.hypot(d[:, 0], d[:, 1]) - r) <= tol * max(1.0, r)
+        if not on.any():
+            continue
+        th = np.arctan2(d[on, 1], d[on, 0])
+        o = np.argsort(th)
+        ids, th = wall[on][o], th[o]
+        if len(th) == 1:
+            gaps = np.array([2 * np.pi])
+        else:
+            nxt = np.roll(th, -1) - th
+            nxt[-1] += 2 * np.pi
+            gaps = 0.5 * (nxt + np.roll(nxt, 1))
+        nodes.append(ids)
+        nrm.append(np.stack([np.cos(th), np.sin(th)], 1))
+        ds.append(gaps * r)
+    # straight solid sides: (side index, coordinate axis, wall position, normal)
+    for side, axis, pos, nv in ((2, 1, y0, (0.0, 1.0)), (3, 1, y1, (0.0, -1.0)),
+                                (0, 0, x0, (1.0, 0.0)), (1, 0, x1, (-1.0, 0.0))):
+        if w.sides[side] != SOLID:
+            continue
+        on = np.abs(w.xy[wall, axis] - pos) <= tol * max(1.0, abs(pos))
+        if not on.any():
+            continue
+        t = w.xy[wall[on], 1 - axis]
+        o = np.argsort(t)
+        ids, t = wall[on][o], t[o]
+        length = lx if axis == 1 else ly
+        periodic = per_x if axis == 1 else per_y
+        if periodic:
+            nxt = np.roll(t, -1) - t
+            nxt[-1] += length
+            gaps = 0.5 * (nxt + np.roll(nxt, 1))
+        else:
+            lo, hi = (x0, x1) if axis == 1 else (y0, y1)
+            edges = np.concatenate([[lo], 0.5 * (t[1:] + t[:-1]), [hi]])
+            gaps = np.diff(edges)
+        nodes.append(ids)
+        nrm.append(np.tile(np.array(nv), (len(ids), 1)))
+        ds.append(gaps)
+    if not nodes:
+        return np.zeros(0, np.int64), np.zeros((0, 2)), np.zeros(0)
+    return (np.concatenate(nodes).astype(np.int64), np.concatenate(nrm, 0), np.concatenate(ds))
+
+
 # --------------------------------------------------------------------------
 # Random arrays (initial perturbations, feature noise); no physics
 # --------------------------------------------------------------------------

@@ -84,6 +84,7 @@ def lib():
                 "mlbm_step_count": (_i64, [_vp]),
                 "mlbm_macroscopics": (st, [_vp, _vp, _vp]),
                 "mlbm_drag_lift": (st, [_vp, _dbl, _dbl, _vp, _vp, _vp, _vp]),
+                "mlbm_wall_stress_force": (st, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
                 "mlbm_permeability": (st, [_vp, _vp, _vp, _vp, _vp]),
                 "mlbm_run_to_steady": (st, [_vp, _dbl, _i64, _i64, _vp]),
                 "mlbm_run_to_steady_ex": (st, [_vp, _dbl, _i64, _i64, _i64, _vp]),
@@ -317,6 +318,21 @@ def drag_lift(ctx: Context, ref_length: float = 1.0, u_ref: float = 1.0):
     v = [ctypes.c_double() for _ in range(4)]
     _check(lib().mlbm_drag_lift(ctx.handle, float(ref_length), float(u_ref), *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def wall_stress_force(ctx: Context, nodes, normals, ds) -> tuple:
+    """Force (fx, fy) of the fluid on the walls by integrating the fluid
+    stress along the listed wall nodes (caller's ids), with unit normals out of
+    the solid and wall lengths per node; see inputs.wall_geometry."""
+    nodes = np.ascontiguousarray(nodes, np.int64)
+    normals = _f64(np.asarray(normals, np.float64).reshape(-1, 2))
+    ds = _f64(ds)
+    if not (len(nodes) == len(normals) == len(ds)):
+        raise ValueError("nodes, normals and ds must have the same length")
+    fx, fy = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mlbm_wall_stress_force(ctx.handle, _ptr(nodes), _ptr(normals), _ptr(ds), len(nodes),
+                                        ctypes.byref(fx), ctypes.byref(fy)))
+    return fx.value, fy.value
 
 
 def permeability(ctx: Context):

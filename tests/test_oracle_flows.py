@@ -280,7 +280,7 @@ def _square_array_k(L, a):
     return L * L * (-0.5 * np.log(c) - 0.738 + c - 0.887 * c * c + 2.039 * c ** 3) / (4 * np.pi)
 
 
-def _steady_k(w, L, g=1e-6, chunk=2000, max_steps=80_000):
+def _steady_k(w, L, g=1e-6, chunk=2000, max_steps=80_000, full=False):
     op = O.Operator(w, K=16, s=1.0, bb_mode=1).check()
     ru = np.zeros((w.n, 3))
     ru[:, 0] = 1.0
@@ -290,7 +290,7 @@ def _steady_k(w, L, g=1e-6, chunk=2000, max_steps=80_000):
         us, _ = O.mean_velocity(ru[:, 1], w.area, None, total_area=L * L)
         k = O.permeability(us, 1.0, g)
         if k_old is not None and abs(k / k_old - 1) < 1e-8:
-            return k
+            return (k, op, ru) if full else k
         k_old = k
     raise AssertionError("no steady state")
 
@@ -304,15 +304,44 @@ def test_square_cylinder_array_permeability_converges_to_closed_form():
     spacings; the bounds leave room around those, and the error must fall
     as the resolution rises.  A wrong force or viscosity factor fails every
     bound; whole-cell node areas instead of the fluid-Voronoi ones give 1.2%
-    below at radius 16 and fail the finest."""
-    errs = []
-    for L, a, bound in ((20.0, 4.0, 0.025), (40.0, 8.0, 0.012), (80.0, 16.0, 0.005)):
-        k = _steady_k(I.cylinder_array(L, a, seed=1), L)
+    below at radius 16 and fail the finest.  The same steady fields pin the
+    wall force from the integrated stress: it must carry the body force on
+    the fluid, converging as the resolution rises."""
+    errs, ferrs = [], []
+    for L, a, bound, fbound in ((20.0, 4.0, 0.025, 0.08), (40.0, 8.0, 0.012, 0.045), (80.0, 16.0, 0.005, 0.025)):
+        w = I.cylinder_array(L, a, seed=1)
+        k, op, ru = _steady_k(w, L, full=True)
         e = abs(k / _square_array_k(L, a) - 1)
         assert e <= bound, (L, a, k, e)
         errs.append(e)
+        # steady momentum balance: the stress integrated along the disk carries
+        # the body force on the fluid (the oracle's stress-integration force;
+        # 6.3%, 3.2% and 1.5% low at radii 4, 8 and 16)
+        fx, fy = O.wall_stress_force(op, ru, 1.0, *I.wall_geometry(w))
+        body = 1e-6 * np.sum(ru[:, 0] * w.area)
+        fe = abs(fx / body - 1)
+        assert fe <= fbound and abs(fy) <= 0.02 * body, (L, a, fx / body, fy / body)
+        ferrs.append(fe)
     assert errs[0] > errs[1] > errs[2], errs
+    assert ferrs[0] > ferrs[1] > ferrs[2], ferrs
     # a dilute array (c = 0.031), radius 8
     L, a = 80.0, 8.0
     k = _steady_k(I.cylinder_array(L, a, seed=1), L)
     assert abs(k / _square_array_k(L, a) - 1) <= 0.008, k
+
+
+def test_wall_geometry_lengths_and_normals():
+    """The wall lengths of the nodes on a disk add up to its perimeter and
+    those on a straight solid side to the side's length; normals are unit
+    vectors pointing out of the solid."""
+    w = I.cylinder_array(40.0, 8.0, seed=1)
+    nodes, nrm, ds = I.wall_geometry(w)
+    assert abs(ds.sum() - 2 * np.pi * 8.0) < 1e-9
+    d = w.xy[nodes] - np.array([20.0, 20.0])
+    assert np.allclose(np.hypot(*nrm.T), 1.0)
+    assert np.allclose(d / 8.0, nrm, atol=1e-9)
+    w = I.poiseuille_channel(40, 50, 0.2, seed=1)
+    nodes, nrm, ds = I.wall_geometry(w)
+    bottom = nrm[:, 1] > 0
+    assert abs(ds[bottom].sum() - 40.0) < 1e-9 and abs(ds[~bottom].sum() - 40.0) < 1e-9
+    assert np.allclose(w.xy[nodes[bottom], 1], 0.0) and np.allclose(w.xy[nodes[~bottom], 1], 49.0)
