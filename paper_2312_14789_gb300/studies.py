@@ -421,7 +421,9 @@ def lbm_study(args):
     meshless step on the scattered, the hybrid and the coarsened hybrid
     (spacing 2 beyond 2 D) node sets.  Per method:
     nodes, time per step (CUDA events, back to back), algorithmic bytes per
-    step, Strouhal number and mean drag over the second half of --steps."""
+    step, Strouhal number and mean drag over the second half of --steps (for
+    the meshless sets from the momentum exchange and from the stress
+    integrated along the cylinder's wall nodes)."""
     import torch
     from paper_2312_14789_gb300 import inputs as I
     from paper_2312_14789_gb300 import mlbm
@@ -476,14 +478,20 @@ def lbm_study(args):
         us = timed(lambda k: mlbm.step(ctx, k), stream)
         ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0))
         mlbm.set_kernel_variant(ctx, variant)
+        geo = I.wall_geometry(w)
+        cd_st, cl_st = np.empty(len(cd)), np.empty(len(cd))
         for i in range(len(cd)):
             mlbm.step(ctx, every)
             _, _, cd[i], cl[i] = mlbm.drag_lift(ctx, d, u0)
+            fx, fy = mlbm.wall_stress_force(ctx, *geo)
+            cd_st[i], cl_st[i] = 2 * fx / (u0 ** 2 * d_lb), 2 * fy / (u0 ** 2 * d_lb)
         import bench
         out[name] = {"nodes": int(w.n), "n_lagrange": info["n_lagrange"], "variant": variant, "us_per_step": us,
                      "mnups": w.n / us, "algorithmic_bytes_per_step": int(bench.algorithmic_bytes(info, 16)),
                      "strouhal": _strouhal(cl[h:], every, d_lb, u0), "cd_mean": float(np.mean(cd[h:])),
-                     "cl_amplitude": float(np.ptp(cl[h:]) / 2)}
+                     "cl_amplitude": float(np.ptp(cl[h:]) / 2),
+                     "cd_mean_stress": float(np.mean(cd_st[h:])), "cl_amplitude_stress": float(np.ptp(cl_st[h:]) / 2),
+                     "strouhal_stress": _strouhal(cl_st[h:], every, d_lb, u0)}
         print(json.dumps(out[name]), file=sys.stderr, flush=True)
     for name in ("meshless_scattered", "meshless_hybrid", "meshless_hybrid_coarse"):
         out[name]["time_per_step_over_lattice"] = out[name]["us_per_step"] / out["lattice"]["us_per_step"]
