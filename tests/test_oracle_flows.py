@@ -345,6 +345,12 @@ def test_wall_geometry_lengths_and_normals():
     bottom = nrm[:, 1] > 0
     assert abs(ds[bottom].sum() - 40.0) < 1e-9 and abs(ds[~bottom].sum() - 40.0) < 1e-9
     assert np.allclose(w.xy[nodes[bottom], 1], 0.0) and np.allclose(w.xy[nodes[~bottom], 1], 49.0)
+    # porous box: disks that cross the periodic side count once, with their images
+    w = I.porous(seed=5, n_target=15000)
+    nodes, nrm, ds = I.wall_geometry(w)
+    walls = 2 * (w.box[2] - w.box[0])
+    assert abs(ds.sum() - (2 * np.pi * w.disks[:, 2].sum() + walls)) < 1e-6
+    assert len(np.unique(nodes)) == len(nodes) == int(np.sum(w.node_class == I.WALL))
 
 
 def test_wall_stress_force_balances_body_force_in_the_jittered_channel():
