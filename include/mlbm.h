@@ -321,8 +321,10 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        the tau = 1 model runs variant 11 for these numbers)
  *   18-19 as 10 without the bounce-back code (fewer registers), registers
  *        capped for 2 / 3 resident blocks of 256, followed by a second kernel
- *        that recomputes every node with bounce-back links in full and
- *        overwrites its output (BGK only; tau = 1 runs variant 11)
+ *        that recomputes every node with bounce-back links (16 lanes per node,
+ *        one gather per stencil member for both the departure values and the
+ *        link fits) and overwrites its output (BGK only; tau = 1 runs
+ *        variant 11)
  *   20-21 as 11 (plain grid, capped for 2 blocks) and as 10 (persistent,
  *        uncapped), with the first three index rows and the rest population
  *        loaded before the node kind is read, so their latency overlaps the
