@@ -62,6 +62,7 @@ struct mlbm_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = -1.0;
     int variant = 25;
+    std::vector<int> inv_perm;  // caller's node id -> device position
     int* err = nullptr;  // device error word of the bounded waits
     dev::Stencil S{};
     dev::Collide C{};
@@ -254,6 +255,8 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
         }
     }
     c->n_link_nodes = (int)hlinknodes.size();
+    c->inv_perm.assign((size_t)n, -1);
+    for (int64_t q = 0; q < n; ++q) c->inv_perm[(size_t)hperm[q]] = (int)q;
     // ---- neighbourhood staging (variant 22, least-squares BGK): per tile of
     // kStageTile nodes the sorted union of the stencil members of its
     // least-squares nodes without links, and each member's local index
@@ -672,14 +675,10 @@ mlbm_status mlbm_wall_stress_force(mlbm_ctx* c, const int64_t* nodes, const doub
     if (c->S.Wr) return set_error(MLBM_E_INVALID, "wall_stress_force: least-squares stencils only");
     if (m > (int64_t)1 << 30) return set_error(MLBM_E_INVALID, "wall_stress_force: too many wall nodes");
     // caller's node ids -> device positions
-    std::vector<int> perm((size_t)c->n_pad), pos((size_t)m);
-    MLBM_CUDA(cudaMemcpyAsync(perm.data(), c->perm, (size_t)c->n_pad * 4, cudaMemcpyDeviceToHost, c->stream));
-    MLBM_TRY(sync(c));
-    std::vector<int> inv((size_t)c->n, -1);
-    for (int64_t q = 0; q < c->n; ++q) inv[(size_t)perm[(size_t)q]] = (int)q;
+    std::vector<int> pos((size_t)m);
     for (int64_t i = 0; i < m; ++i) {
         if (nodes[i] < 0 || nodes[i] >= c->n) return set_error(MLBM_E_INVALID, "wall_stress_force: node id out of range");
-        pos[(size_t)i] = inv[(size_t)nodes[i]];
+        pos[(size_t)i] = c->inv_perm[(size_t)nodes[i]];
     }
     double sx = 0.0, sy = 0.0;
     if (m > 0) {
