@@ -9,13 +9,15 @@ Re in {100, 200} x streaming distance s in {1/2, 1/4, 1/8} node spacings
 (D = 80, 160, 320 lattice units, U0 = 0.05, tau = 3 U0 D / Re + 1/2), all six
 advanced together in one batched context (one fused launch per time step,
 replayed from captured CUDA graphs).  One bench "step" = one time step of all
-six runs = 6 x 259,887 node updates.  The working set (~780 MB) is larger
+six runs = 6 x 259,971 node updates.  The working set (~780 MB) is larger
 than L2, so consecutive steps are timed back to back without a flush.
 
 Arms:
   default            the CUDA path through the C ABI (device-resident state)
   --impl reference   the FP64 CPU oracle on a bounded node sample (the
-                     reference arm of this build; no GPU)
+                     reference arm; no GPU)
+  --variant V        a fixed step kernel variant (and --node-order) instead
+                     of the autotuner, for profiler runs
 Output: one JSON line on rank 0.
 """
 from __future__ import annotations
