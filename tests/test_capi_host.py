@@ -143,3 +143,14 @@ def test_builder_rbf_weights_match_oracle(case):
         interp_k = sel & ~((op.link[:, k] != 0) & (bb == 0))
         err = np.abs(W[interp_k, k] - op.W[interp_k, k]).max()
         assert err < 1e-8, (k, err)
+
+
+def test_context_calls_reject_null_arguments_without_a_device():
+    """Argument checks come before any device work: a NULL context gives
+    MLBM_E_INVALID (1) from the calls that take one."""
+    L = mlbm.lib()
+    d = np.zeros(2)
+    assert L.mlbm_wall_stress_force(None, None, None, None, 0, d.ctypes.data, d.ctypes.data + 8) == 1
+    assert L.mlbm_step(None, 1) == 1
+    assert L.mlbm_drag_lift(None, 1.0, 1.0, None, None, None, None) == 1
+    assert L.mlbm_permeability(None, None, None, None, None) == 1
