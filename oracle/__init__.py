@@ -15,6 +15,7 @@ Main entry points
   macroscopics(f, g)                 rho, u of a post-collision state
   force_bgk / force_mlbm1            momentum exchange on the solids
   mean_velocity, permeability, tortuosity, strouhal, memory model
+  steady_mean_step, paper_time_step   the steady criterion of Sec. 3.2
 """
 from __future__ import annotations
 
@@ -403,6 +404,37 @@ def strouhal(cl, dt_per_sample, diameter_lb, u0, min_periods=2):
     tz = (i + (-c[i]) / (c[i + 1] - c[i])) * dt_per_sample
     period = float(np.mean(np.diff(tz)))
     return (1.0 / period) * diameter_lb / u0
+
+
+def paper_time_step(tau, s, box_side):
+    """Physical time of one step in the units of Sec. 3.2 (sample side length
+    1, kinematic viscosity 1): nu_phys = nu_lb dx^2 / dt with the streaming
+    distance dx = s / box_side in those units and nu_lb = (tau - 1/2)/3
+    (Eq. (6)), hence dt = nu_lb (s / box_side)^2."""
+    return (tau - 0.5) / 3.0 * (s / box_side) ** 2
+
+
+def steady_mean_step(mean_u, check, dn, dt, threshold):
+    """The steady-state criterion of Sec. 3.2 applied to a record of the mean
+    x-velocity: mean_u[j] is <u> at step j*check (j = 0, 1, ...).  At every
+    recorded step t >= dn the relative rate of change over the previous dn
+    steps is
+        Delta u = (<u>(t) - <u>(t - dn)) / (<u>(t - dn) dt dn),
+    the earlier mean <u>^n in the denominator as the paper prints it, taken in
+    absolute value (reading: a mean that approaches its limit from above must
+    not count as steady at once).  Returns the first such t with
+    Delta u < threshold, or -1.  A zero earlier mean is never steady."""
+    if dn % check:
+        raise ValueError("dn must be a multiple of check")
+    lag = dn // check
+    for j in range(lag, len(mean_u)):
+        then, now = float(mean_u[j - lag]), float(mean_u[j])
+        if then == 0.0:
+            continue
+        rate = abs(now - then) / (abs(then) * dt * dn)
+        if rate < threshold:
+            return j * check
+    return -1
 
 
 def relative_l2(a, b):
