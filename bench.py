@@ -1,23 +1,41 @@
-"""Benchmark of the fused MLBM step on the vortex-street configuration.
+"""Benchmark of the fused MLBM step and of the time to steady state.
 
-Workload: the Karman vortex street configuration as a whole -- a channel
-22D x 4.1D around a cylinder of diameter D = 40 node spacings, ~260k
-scattered Poisson-disk nodes refined near the cylinder (seed 2), K = 16
-least-squares stencils, BGK in FP32, simple bounce-back on the cylinder,
-equilibrium inflow/outflow/side nodes -- run for its six (Re, s) cases
-Re in {100, 200} x streaming distance s in {1/2, 1/4, 1/8} node spacings
-(D = 80, 160, 320 lattice units, U0 = 0.05, tau = 3 U0 D / Re + 1/2), all six
-advanced together in one batched context (one fused launch per time step,
-replayed from captured CUDA graphs).  One bench "step" = one time step of all
-six runs = 6 x 259,971 node updates.  The working set (~780 MB) is larger
-than L2, so consecutive steps are timed back to back without a flush.
+Default workload (`--workload porous_batch`): the batched porous
+configuration of Sec. 3.2's flow through a porous sample -- 64 independent
+samples (seeds 1000..1063), each a square box of random non-overlapping
+solid disks (radii U(8, 16) spacings) with node count U(50k, 400k) and
+porosity U(0.5, 0.85), periodic in x with solid walls top and bottom, K = 16
+least-squares stencils, interpolated bounce-back, the tau = 1 model (MLBM1:
+only rho and u stored) in FP32, streaming distance cycling {1, 1/2, 1/4} and
+body force {1e-6, 5e-6, 2e-5} (Darcy and inertial samples mixed); all 64 in
+one batched context, one fused launch per time step replayed from captured
+CUDA graphs, kernel variant picked by the library's autotuner.  One bench
+"step" is one time step of every sample (~13M node updates).  The working
+set (~6 GB) is far larger than L2, so steps are timed back to back without
+a flush.  Graph capture and instantiation happen before the timed region.
+
+After the timed steps (N = 1 only) the time-to-steady legs run on held-out
+porous samples of the learned warm-start configuration (porosity 0.7,
+~192k nodes, s = 1, g = 1e-6, seeds 20000..): cold single-instance runs,
+one cold batched run, a learned warm start (network trained here, on the
+GPU, on cold-solved training samples, seeds 10000..) batched and single,
+each to |u(t) - u(t-1000)| / (1000 |u(t)|) < 1e-7 checked every 100 steps,
+plus the paper's own criterion (Sec. 3.2: relative change of the mean
+velocity over 2e4 steps per unit time below 1e-2) on the cold batch.
+
+`--workload karman_sweep`: the vortex-street sweep (channel 22D x 4.1D, D =
+40 spacings, ~260k nodes, BGK, simple bounce-back; the six runs Re in
+{100, 200} x s in {1/2, 1/4, 1/8} in one batched context).
 
 Arms:
   default            the CUDA path through the C ABI (device-resident state)
-  --impl reference   the FP64 CPU oracle on a bounded node sample (the
-                     reference arm; no GPU)
-  --variant V        a fixed step kernel variant (and --node-order) instead
-                     of the autotuner, for profiler runs
+  --impl reference   the FP64 CPU oracle on a bounded node sample of the
+                     same workload (the reference arm; no GPU)
+  --variant V        a fixed step kernel variant instead of the autotuner
+Multi-GPU (torchrun): every rank owns whole samples and nothing is exchanged
+while stepping; `--scaling weak` (default) gives every rank its own 64
+samples (seeds offset by the rank), `--scaling strong` splits the one set of
+64 among the ranks, balanced by node count.
 Output: one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -38,63 +56,64 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mnode-updates/s (FP32, err vs FP64 stated); time-to-steady warm vs cold"
 UNIT = "Mnode-updates/s"
+ORDER_NAMES = ["hilbert", "morton", "rows", "input"]
+
+# vortex-street sweep
 U0, D = 0.05, 40.0
 CASES = [(re, s) for re in (100, 200) for s in (0.5, 0.25, 0.125)]
+
+# time-to-steady legs (criterion of the learned warm-start configuration)
+TOL, WINDOW, CHECK = 1e-7, 1000, 100
+PAPER_THRESHOLD, PAPER_DN, PAPER_CHECK = 1e-2, 20000, 1000
 
 
 def tau_of(re, s):
     return 3.0 * U0 * (D / s) / re + 0.5
 
 
-WORKLOAD = {"workload": "karman_vortex_street_sweep", "runs": [{"Re": re, "s": s, "tau": round(tau_of(re, s), 4)}
-                                                               for re, s in CASES],
-            "nodes_per_run": None, "node_updates_per_step": None, "K": 16, "model": "BGK", "D_spacings": 40,
-            "U0": U0, "seed": 2, "bounce_back": "simple",
-            "l2": "working set ~780 MB > L2; steps timed back to back"}
-TAU, S_STREAM = tau_of(100, 0.5), 0.5
-PROFILE = os.path.join(ROOT, "profiles", "bgk_step_karman_sweep.md")
-
-
-def algorithmic_bytes(info, K):
-    """Bytes one fused step must move at minimum, per node kind: least-squares
-    node 4*(9+9) populations + 4*6K matrix + 4K indices + 1 meta; Lagrange
-    node 4*(9+9) + 4*12 indices + 4 (s/h) + 1; equilibrium node 16 + 36 + 1."""
-    wls = 4 * 18 + 4 * 6 * K + 4 * K + 1
-    lag = 4 * 18 + 4 * 12 + 4 + 1
-    eq = 16 + 36 + 1
+def algorithmic_bytes(info, K, model="bgk"):
+    """Bytes one fused step must move at minimum, per node kind.
+    BGK: least-squares node 4*(9+9) populations + 4*6K matrix + 4K indices +
+    1 meta; Lagrange node 4*(9+9) + 4*12 indices + 4 (s/h) + 1; equilibrium
+    node 16 + 36 + 1.  tau = 1: the state is (rho, u_x, u_y), 3 floats read
+    and 3 written, so 4*(3+3) replaces 4*(9+9) and an equilibrium node costs
+    12 + 12 + 1 (the 16-byte padding of the stored state is not the method's
+    work and is not counted)."""
+    state = 4 * 6 if model == "tau1" else 4 * 18
+    wls = state + 4 * 6 * K + 4 * K + 1
+    lag = state + 4 * 12 + 4 + 1
+    eq = 12 + 12 + 1 if model == "tau1" else 16 + 36 + 1
     return info["n_wls"] * wls + info["n_lagrange"] * lag + info["n_eq"] * eq
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "device_common.cuh"):
+    for f in ("kernels.cu", "kernels_tma.cu", "device_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2312_14789_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-ORDER_NAMES = ["hilbert", "morton", "rows", "input"]
+TRAFFIC = {"porous_batch": os.path.join(ROOT, "profiles", "tau1_step_porous_batch.json"),
+           "karman_sweep": os.path.join(ROOT, "profiles", "bgk_step_karman_sweep.json")}
 
 
-def measured_traffic(variant, order=0):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when it was taken on a different kernel source, variant or node
-    order."""
+def measured_traffic(workload, variant, order=0, node_updates=None):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    record of this workload (profiles/*.json, written from an ncu capture),
+    or None when it was taken on another kernel source, variant or node
+    order.  A record taken on a smaller case of the same kernel is scaled to
+    this launch by the node updates it processes."""
     try:
-        txt = open(PROFILE).read()
-    except OSError:
+        rec = json.load(open(TRAFFIC[workload]))
+    except (OSError, KeyError, ValueError):
         return None
-    vals = {}
-    for line in txt.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_hash") != kernel_source_hash() or vals.get("kernel_variant") != str(variant) \
-            or vals.get("node_order", "hilbert") != ORDER_NAMES[order]:
+    if rec.get("kernel_source_hash") != kernel_source_hash() or rec.get("kernel_variant") != variant \
+            or rec.get("node_order", "hilbert") != ORDER_NAMES[order]:
         return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    t = float(rec["dram_bytes_per_launch"])
+    if node_updates and rec.get("node_updates_per_launch"):
+        t *= node_updates / float(rec["node_updates_per_launch"])
+    return t
 
 
 def peaks():
@@ -105,7 +124,9 @@ def peaks():
 
 
 class Clocks:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi sampled every 50 ms; samples at >= 50% utilisation count
+    as under load."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -113,7 +134,7 @@ class Clocks:
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -121,81 +142,157 @@ class Clocks:
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.p.terminate()
         out, _ = self.p.communicate(timeout=10)
-        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 6]
-        sm, mx, reasons = [], None, set()
+        return self.parse(out)
+
+    @staticmethod
+    def parse(out):
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 7]
+        sm_all, sm_load, mx, reasons = [], [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             try:
-                sm.append(float(r[0]))
-                mx = float(r[1])
+                sm, mx, util = float(r[0]), float(r[1]), float(r[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, r[3:7]):
+            sm_all.append(sm)
+            if util >= 50:
+                sm_load.append(sm)
+            for nm, v in zip(names, r[4:8]):
                 if v.strip().lower() == "active":
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        use = sm_load or sm_all
+        return {"sm_mhz": statistics.median(use) if use else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm_all), "samples_under_load": len(sm_load)}
 
 
-def make_workload():
+# ------------------------------------------------------------------ workloads
+def porous_specs(args, rank, world):
+    """This rank's sample specs and the assignment (strong scaling) or seed
+    offset (weak scaling)."""
     from paper_2312_14789_gb300 import inputs as I
-    return I.karman(seed=2)
+    from paper_2312_14789_gb300 import shard
+    if args.scaling == "strong" and world > 1:
+        specs = I.porous_batch_specs(args.samples)
+        assignment = shard.assign_balanced([s["n_target"] for s in specs], world)
+        return [specs[i] for i in assignment[rank]], assignment
+    first = 1000 + shard.rank_seed_offset(rank, args.samples)
+    return I.porous_batch_specs(args.samples, first_seed=first), None
 
 
-def oracle_sample_rate(w, n_sample, seed, min_seconds, max_reps):
-    """Time the oracle's BGK step on n_sample nodes of the workload; returns
-    (Mnode-updates/s, threads, description)."""
+def make_inputs(args, rank, world):
+    """Node sets of this rank (spawned worker processes; called before CUDA
+    is touched)."""
+    from paper_2312_14789_gb300 import inputs as I
+    if args.workload == "karman_sweep":
+        return {"karman": I.karman(seed=2)}
+    specs, assignment = porous_specs(args, rank, world)
+    out = {"specs": specs, "assignment": assignment, "batch": I.generate(specs)}
+    if rank == 0 and world == 1 and args.steady:
+        test = [{"seed": 20000 + i, "n_target": 200_000, "porosity": 0.7} for i in range(args.steady_samples)]
+        train = [{"seed": 10000 + i, "n_target": args.train_nodes, "porosity": 0.7}
+                 for i in range(args.train_samples)]
+        ws = I.generate(test + train)
+        out["steady_test"], out["steady_train"] = ws[:len(test)], ws[len(test):]
+    return out
+
+
+def build_batch(args, inputs):
+    """Stencils, params and per-sample byte counts of the timed batch."""
+    from paper_2312_14789_gb300 import mlbm
+    if args.workload == "karman_sweep":
+        w = inputs["karman"]
+        st_by_s = {s: mlbm.build_stencils_for(w, K=16, s=s, bb_mode=mlbm.BB_SIMPLE)
+                   for s in sorted({s for _, s in CASES})}
+        sts = [st_by_s[s] for _, s in CASES]
+        params = [mlbm.Params(mlbm.MODEL_BGK, tau_of(re, s), 0.0, 0.0, 0.0) for re, s in CASES]
+        return sts, params, "bgk", list(st_by_s.values())
+    sts = [mlbm.build_stencils_for(w, K=16, s=sp["s"], bb_mode=mlbm.BB_INTERPOLATED)
+           for w, sp in zip(inputs["batch"], inputs["specs"])]
+    params = [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, sp["g"], 0.0) for sp in inputs["specs"]]
+    return sts, params, "tau1", sts
+
+
+def workload_config(args, inputs, infos, n, world):
+    if args.workload == "karman_sweep":
+        w = inputs["karman"]
+        return {"workload": "karman_vortex_street_sweep",
+                "runs": [{"Re": re, "s": s, "tau": round(tau_of(re, s), 4)} for re, s in CASES],
+                "nodes_per_run": w.n, "K": 16, "model": "BGK", "D_spacings": 40, "U0": U0, "seed": 2,
+                "bounce_back": "simple", "node_updates_per_step": n,
+                "l2": "working set ~780 MB > L2 (129 MB): steps timed back to back, no flush"}
+    ws = inputs["batch"]
+    return {"workload": "porous_batch_64" if args.samples == 64 else f"porous_batch_{args.samples}",
+            "samples_per_rank": len(ws), "seeds": [sp["seed"] for sp in inputs["specs"]][:1] +
+            [sp["seed"] for sp in inputs["specs"]][-1:],
+            "nodes_range": [min(w.n for w in ws), max(w.n for w in ws)],
+            "porosity_range": [round(min(w.meta["porosity"] for w in ws), 4),
+                               round(max(w.meta["porosity"] for w in ws), 4)],
+            "s_cycle": [1.0, 0.5, 0.25], "g_cycle": [1e-6, 5e-6, 2e-5], "K": 16, "model": "MLBM1 (tau = 1)",
+            "bounce_back": "interpolated", "node_updates_per_step": n,
+            "l2": "working set ~6 GB > L2 (129 MB): steps timed back to back, no flush"}
+
+
+# ---------------------------------------------------------------- reference
+def oracle_sample_rate(args, inputs, n_sample, seed, min_seconds=0.0, max_reps=1, reps=None):
+    """Time the oracle's step on a random sample of n_sample nodes of one
+    sample of the workload (a sampled rate: the gathers of scattered targets
+    miss cache more often than an in-order sweep would).  Runs exactly `reps`
+    steps when given, else until min_seconds have passed (at most max_reps).
+    Returns (Mnode-updates/s, threads, description, seconds per step)."""
     import oracle as O
     rng = np.random.default_rng(seed)
-    t = np.sort(rng.choice(w.n, size=n_sample, replace=False))
-    op = O.Operator(w, K=16, s=S_STREAM, bb_mode=0, targets=t).check()
-    f = O.equilibrium(np.ones(w.n), 0.0, 0.0)
-    reps, elapsed = 0, 0.0
-    while reps < max_reps and (elapsed < min_seconds or reps == 0):
+    if args.workload == "karman_sweep":
+        w, s, model = inputs["karman"], 0.5, "bgk"
+        what = f"the {w.n}-node vortex-street node set (Re = 100, s = 1/2)"
+    else:
+        i = int(np.argsort([w.n for w in inputs["batch"]])[len(inputs["batch"]) // 2])
+        w, s, model = inputs["batch"][i], inputs["specs"][i]["s"], "tau1"
+        what = f"porous sample seed {inputs['specs'][i]['seed']} ({w.n} nodes, s = {s})"
+    t = np.sort(rng.choice(w.n, size=min(n_sample, w.n), replace=False))
+    op = O.Operator(w, K=16, s=s, bb_mode=0 if model == "bgk" else 1, targets=t).check()
+    if model == "bgk":
+        state = O.equilibrium(np.ones(w.n), 0.0, 0.0)
+        step = lambda: O.bgk_step(op, state, tau_of(100, 0.5))
+    else:
+        state = np.zeros((w.n, 3))
+        state[:, 0] = 1.0
+        step = lambda: O.mlbm1_step(op, state, (1e-6, 0.0))
+    per = []
+    while (len(per) < reps) if reps is not None else (len(per) < max_reps and (sum(per) < min_seconds or not per)):
         t0 = time.perf_counter()
-        O.bgk_step(op, f, TAU)
-        elapsed += time.perf_counter() - t0
-        reps += 1
+        step()
+        per.append(time.perf_counter() - t0)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return n_sample * reps / elapsed / 1e6, threads, f"{n_sample} random nodes of the {w.n}-node workload x {reps} steps"
+    return (len(t) * len(per) / sum(per) / 1e6, threads,
+            f"sampled rate: {len(t)} random nodes of {what} x {len(per)} steps", per)
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = make_workload()
-    per_step = []
-    import oracle as O
-    rng = np.random.default_rng(0)
-    n_sample = 4096
-    t = np.sort(rng.choice(w.n, size=n_sample, replace=False))
-    op = O.Operator(w, K=16, s=S_STREAM, bb_mode=0, targets=t).check()
-    f = O.equilibrium(np.ones(w.n), 0.0, 0.0)
-    # one of the six runs (Re = 100, s = 1/2); the others cost the same per node
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        O.bgk_step(op, f, TAU)
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            per_step.append(dt)
-    total = sum(per_step)
-    value = n_sample * args.steps / total / 1e6
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    cfg = dict(WORKLOAD, nodes_per_run=w.n, node_updates_per_step=w.n * len(CASES))
+    inputs = make_inputs(argparse.Namespace(**{**vars(args), "steady": False}), 0, 1)
+    if args.workload == "karman_sweep":
+        n = inputs["karman"].n * len(CASES)
+    else:
+        n = sum(w.n for w in inputs["batch"])
+    oracle_sample_rate(args, inputs, 4096, 0, reps=args.warmup)              # untimed warm-up steps
+    value, threads, desc, per = oracle_sample_rate(args, inputs, 4096, 0, reps=args.steps)
+    total = sum(per)
+    cfg = workload_config(args, inputs, None, n, 1)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": cfg,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{n_sample} random nodes of the {w.n}-node vortex-street node set (Re=100, s=1/2) per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
+# ---------------------------------------------------------------- ours
 def max_over_ranks(value, dist, device):
     """The largest of every rank's value (the job's time is its slowest
     rank's); the value itself without a process group."""
@@ -207,13 +304,147 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
+def sum_over_ranks(value, dist, device):
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def whole_job_rate(nodes_per_rank, steps, world, ms):
-    """Mnode-updates/s of the whole job: every rank advances its own replica
-    of the workload (weak scaling), timed by the slowest rank."""
+    """Mnode-updates/s of the whole job when every rank advances the same
+    number of node updates (weak scaling), timed by the slowest rank."""
     return nodes_per_rank * steps * world / (ms / 1e3) / 1e6
 
 
+def job_rate(total_node_updates, ms):
+    """Mnode-updates/s of the node updates of all ranks over the slowest
+    rank's time."""
+    return total_node_updates / (ms / 1e3) / 1e6
+
+
+def steady_legs(inputs, log):
+    """Time to steady state on held-out porous samples: cold single-instance,
+    cold batched, learned warm start (batched and single), and the paper's
+    criterion on the cold batch.  Everything runs through the C ABI; the
+    network is trained here by the library's kernels."""
+    import torch
+    from paper_2312_14789_gb300 import mlbm
+    from paper_2312_14789_gb300 import warmstart as W
+    sync = torch.cuda.synchronize
+    g = 1e-6
+    test, train = inputs["steady_test"], inputs["steady_train"]
+    out = {"criterion": f"|u(t) - u(t-{WINDOW})| / ({WINDOW} |u(t)|) < {TOL:g}, checked every {CHECK} steps",
+           "samples": len(test), "nodes": [w.n for w in test], "s": 1.0, "g": g, "tau": 1.0,
+           "seeds": [int(w.meta["seed"]) for w in test]}
+    t0 = time.perf_counter()
+    sts = W.build(test)
+    out["stencil_build_s"] = time.perf_counter() - t0
+    ps = [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, g, 0.0) for _ in test]
+    n_test = sum(w.n for w in test)
+
+    # cold, single instance (the plain solver a user runs per sample)
+    cold1 = []
+    for st, p in zip(sts, ps):
+        sync()
+        t0 = time.perf_counter()
+        ctx = mlbm.init(st, p)
+        steps = mlbm.run_to_steady(ctx, TOL, WINDOW, 400_000, check=CHECK)
+        k = mlbm.permeability(ctx)["k"]
+        sync()
+        cold1.append({"steps": steps, "s": time.perf_counter() - t0, "k": k})
+        del ctx
+    k_cold = np.array([r["k"] for r in cold1])
+    out["cold_single"] = {"steps": [r["steps"] for r in cold1], "seconds_total": sum(r["s"] for r in cold1),
+                          "mnups": sum(r["steps"] * w.n for r, w in zip(cold1, test)) /
+                          sum(r["s"] for r in cold1) / 1e6}
+    log(f"cold single: {out['cold_single']['seconds_total']:.2f} s")
+
+    # cold, batched (all held-out samples in one context)
+    ru_c, st_c, sec_c, k_c = W.solve(sts, ps, tol=TOL, window=WINDOW, check=CHECK)
+    out["cold_batched"] = {"steps": [int(v) for v in st_c], "seconds": sec_c,
+                           "mnups": n_test * int(max(st_c)) / sec_c / 1e6,
+                           "k_rel_diff_vs_single_max": float(np.max(np.abs(k_c / k_cold - 1)))}
+    log(f"cold batched: {sec_c:.2f} s")
+
+    # learned warm start: training data from cold batched solves of the
+    # training samples, then the network (velocity + density outputs)
+    t0 = time.perf_counter()
+    sts_tr = W.build(train)
+    t_build_tr = time.perf_counter() - t0
+    ps_tr = [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, g, 0.0) for _ in train]
+    ru_tr, steps_tr, sec_tr, _ = W.solve(sts_tr, ps_tr, tol=TOL, window=WINDOW, check=CHECK)
+    del sts_tr
+    X = W.features(train)
+    T = torch.from_numpy(W.targets(train, ru_tr, ps_tr, 3)).cuda()
+    net = mlbm.Mlp(7, 3)
+    sync()
+    t0 = time.perf_counter()
+    losses = W.train(net, X, T, 8000, batch=65536)
+    sync()
+    t_train = time.perf_counter() - t0
+    out["training"] = {"samples": len(train), "rows": int(X.shape[0]),
+                       "nodes_mean": float(np.mean([w.n for w in train])), "seeds_first": int(train[0].meta["seed"]),
+                       "cold_solve_s": sec_tr, "stencil_build_s": t_build_tr, "adam_steps": 8000,
+                       "train_s": t_train, "minibatch_loss_last": losses[-1]}
+    del X, T
+    sync()
+    t0 = time.perf_counter()
+    Xt = W.features(test)
+    sync()
+    t_feat = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ru_w, st_w, sec_w, k_w = W.solve(sts, ps, init=W.warm_init(net, Xt, test, ps), tol=TOL, window=WINDOW,
+                                     check=CHECK)
+    out["warm_batched"] = {"steps": [int(v) for v in st_w], "seconds": sec_w, "features_s": t_feat,
+                           "steps_ratio_over_cold_mean": float(np.mean(np.asarray(st_w, float) /
+                                                                      np.asarray(st_c, float))),
+                           "seconds_ratio_over_cold": (sec_w + t_feat) / sec_c,
+                           "k_rel_diff_vs_cold_max": float(np.max(np.abs(k_w / k_c - 1)))}
+    log(f"warm batched: {sec_w:.2f} s")
+    # learned warm start, single instance (features + inference + solve)
+    warm1 = []
+    for w, st, p in zip(test, sts, ps):
+        sync()
+        t0 = time.perf_counter()
+        ctx = mlbm.init(st, p)
+        Xi = W.features([w])
+        L = W.length_scale(w)
+        mlbm.warm_start(ctx, net, Xi.data_ptr(), W.velocity_scale(g, 1.0, L), W.density_scale(g, L))
+        steps = mlbm.run_to_steady(ctx, TOL, WINDOW, 400_000, check=CHECK)
+        k = mlbm.permeability(ctx)["k"]
+        sync()
+        warm1.append({"steps": steps, "s": time.perf_counter() - t0, "k": k})
+        del ctx, Xi
+    out["warm_single"] = {"steps": [r["steps"] for r in warm1], "seconds_total": sum(r["s"] for r in warm1),
+                          "seconds_ratio_over_cold": sum(r["s"] for r in warm1) / out["cold_single"]["seconds_total"],
+                          "k_rel_diff_vs_cold_max": float(np.max(np.abs(np.array([r["k"] for r in warm1]) /
+                                                                        k_cold - 1)))}
+    # the paper's criterion on the cold batch (Sec. 3.2)
+    ctx = mlbm.batch_init(sts, ps)
+    mlbm.autotune(ctx, 5)
+    mlbm.set_fields(ctx, np.concatenate([np.column_stack([np.ones(w.n), np.zeros(w.n), np.zeros(w.n)])
+                                         for w in test]))
+    sync()
+    t0 = time.perf_counter()
+    st_p = mlbm.batch_run_to_steady_mean(ctx, PAPER_THRESHOLD, PAPER_DN, PAPER_CHECK, None, max_steps=1_000_000)
+    sec_p = time.perf_counter() - t0
+    k_p = mlbm.batch_permeability(ctx)["k"]
+    out["paper_criterion_cold_batched"] = {
+        "criterion": f"|<u>(t) - <u>(t-{PAPER_DN})| / (<u>(t-{PAPER_DN}) dt {PAPER_DN}) < {PAPER_THRESHOLD:g}, "
+                     f"dt = nu (s/L)^2 (side 1, nu = 1), checked every {PAPER_CHECK} steps",
+        "steps": [int(v) for v in st_p], "seconds": sec_p,
+        "k_rel_diff_vs_field_norm_criterion_max": float(np.max(np.abs(k_p / k_c - 1)))}
+    del ctx
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
+    t_setup0 = time.perf_counter()
+    inputs = make_inputs(args, rank, world)      # worker processes, before CUDA is touched
+    t_gen = time.perf_counter() - t_setup0
     import torch
     from paper_2312_14789_gb300 import mlbm
 
@@ -222,88 +453,128 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = make_workload()
-    st_by_s = {s: mlbm.build_stencils_for(w, K=16, s=s, bb_mode=mlbm.BB_SIMPLE) for s in sorted({s for _, s in CASES})}
-    sts = [st_by_s[s] for _, s in CASES]
-    params = [mlbm.Params(mlbm.MODEL_BGK, tau_of(re, s), 0.0, 0.0, 0.0) for re, s in CASES]
+    log = (lambda m: print(m, file=sys.stderr, flush=True)) if rank == 0 else (lambda m: None)
+    t0 = time.perf_counter()
+    sts, params, model, distinct = build_batch(args, inputs)
+    t_build = time.perf_counter() - t0
     infos = [mlbm.stencils_info(st) for st in sts]
+    log(f"inputs {t_gen:.1f} s, stencils {t_build:.1f} s")
+    t0 = time.perf_counter()
     if args.variant >= 0:
-        # fixed choice (for profiler runs, where the tuner's timings are distorted)
         order, variant, tune_ms = ORDER_NAMES.index(args.node_order), args.variant, None
-        for st in st_by_s.values():
+        for st in distinct:
             mlbm.stencils_set_order(st, order)
+        ctx = mlbm.batch_init(sts, params)
+        mlbm.set_kernel_variant(ctx, variant)
+    elif args.tune_order:
+        order, variant, tune_ms = mlbm.autotune_order(sts, params, 5)
+        ctx = mlbm.batch_init(sts, params)
+        mlbm.set_kernel_variant(ctx, variant)
     else:
-        # node order and kernel variant picked together by the library's autotuner
-        order, variant, tune_ms = mlbm.autotune_order(sts, params, 10)
-    ctx = mlbm.batch_init(sts, params)
-    mlbm.set_kernel_variant(ctx, variant)
+        order = ORDER_NAMES.index(args.node_order)
+        for st in distinct:
+            mlbm.stencils_set_order(st, order)
+        ctx = mlbm.batch_init(sts, params)
+        variant, tune_ms = mlbm.autotune(ctx, 5)
     stream = torch.cuda.Stream()
     mlbm.set_stream(ctx, stream.cuda_stream)
+    # one-off setup before the timed region: both step graphs captured and
+    # instantiated for the chosen variant and this stream
+    mlbm.prepare_graphs(ctx)
+    t_tune = time.perf_counter() - t0
     n = ctx.n
     with torch.cuda.stream(stream):
         mlbm.step(ctx, args.warmup)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local_rank) if rank == 0 else None
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local_rank) if rank == 0 else None
-    time.sleep(0.3 if clocks else 0)
+    time.sleep(0.2 if clocks else 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         e0.record(stream)
         mlbm.step(ctx, args.steps)
         e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop() if clocks else None
-    total_ms = max_over_ranks(float(e0.elapsed_time(e1)), dist, "cuda")
+    my_ms = float(e0.elapsed_time(e1))
+    total_ms = max_over_ranks(my_ms, dist, "cuda")
+    total_updates = sum_over_ranks(n * args.steps, dist, "cuda")
     if dist:
         dist.barrier()
-    value = whole_job_rate(n, args.steps, world, total_ms)
+    value = job_rate(total_updates, total_ms)
 
-    # end to end through the public API with host buffers: upload the state
-    # of all six runs from pinned memory, advance, read the fields and the
-    # per-run cylinder forces back
+    # end to end through the public API with host buffers: upload every
+    # sample's state from pinned memory, advance, read the fields and the
+    # per-sample observables back
     e2e_steps = max(args.steps, 1)
-    f_host = torch.empty((n, 9), dtype=torch.float64, pin_memory=True).numpy()
-    f_host[:] = mlbm.get_populations(ctx)
     ru_host = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    ru_host[:] = mlbm.get_fields(ctx)
+    out_host = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
-    mlbm.set_populations(ctx, f_host)
+    mlbm.set_fields(ctx, ru_host)
     mlbm.step(ctx, e2e_steps)
-    r = mlbm.lib().mlbm_get_fields(ctx.handle, ru_host.ctypes.data)
-    forces = mlbm.batch_drag_lift(ctx, D, U0)
-    e2e_s = time.perf_counter() - t0
+    r = mlbm.lib().mlbm_get_fields(ctx.handle, out_host.ctypes.data)
+    if model == "tau1":
+        obs = mlbm.batch_permeability(ctx)["k"]
+    else:
+        obs = mlbm.batch_drag_lift(ctx, D, U0)["cd"]
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     assert r == 0
-    e2e_value = n * e2e_steps * world / e2e_s / 1e6
+    e2e_value = total_updates / args.steps * e2e_steps / e2e_s / 1e6
+    per_sample = [float(v) for v in obs]
+    del ctx
 
+    if dist is not None:
+        gathered = [None] * world
+        dist.all_gather_object(gathered, per_sample)
+        if args.scaling == "strong" and inputs.get("assignment"):
+            from paper_2312_14789_gb300 import shard
+            per_sample = shard.merge_by_sample(gathered, inputs["assignment"], args.samples)
+        else:
+            per_sample = [v for part in gathered for v in part]
+        dist.barrier()
+    steady = None
+    if rank == 0 and world == 1 and args.steady and args.workload == "porous_batch":
+        steady = steady_legs(inputs, log)
+    clk = clocks.stop() if clocks else None
     if rank != 0:
         return
     pk, pk_kind = peaks()
-    bytes_launch = sum(algorithmic_bytes(i, 16) for i in infos)
-    avg_ms = total_ms / args.steps
+    bytes_launch = sum(algorithmic_bytes(i, 16, model) for i in infos)
+    avg_ms = my_ms / args.steps
     achieved = bytes_launch / (avg_ms / 1e3) / 1e9
-    traffic = measured_traffic(variant, order)
-    cpu_val, cpu_threads, cpu_desc = oracle_sample_rate(w, 8192, 1, 10.0, 20000)
-    cfg = dict(WORKLOAD, nodes_per_run=w.n, node_updates_per_step=n, parallelism=f"replicas x{world}",
-               n_wls=int(sum(i["n_wls"] for i in infos)), n_eq=int(sum(i["n_eq"] for i in infos)),
-               n_links=int(sum(i["n_links"] for i in infos)), kernel_variant=variant, node_order=ORDER_NAMES[order],
-               autotune_ms_per_step=tune_ms, cuda_graph_chunk=16)
+    traffic = measured_traffic(args.workload, variant, order, n)
+    cpu_val, cpu_threads, cpu_desc, _ = oracle_sample_rate(args, inputs, 8192, 1, min_seconds=10.0, max_reps=20000)
+    cfg = dict(workload_config(args, inputs, infos, n, world), parallelism=(
+        f"{world} ranks x own samples (weak)" if args.scaling == "weak" else f"{args.samples} samples split over "
+        f"{world} ranks (strong)"), kernel_variant=variant, node_order=ORDER_NAMES[order],
+        autotune_ms_per_step=tune_ms, cuda_graph_chunk=16,
+        n_wls=int(sum(i["n_wls"] for i in infos)), n_links=int(sum(i["n_links"] for i in infos)))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": args.scaling, "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "note": f"algorithmic bytes {bytes_launch} per launch; peak {pk_kind} (burst copy)"},
+                     "note": f"rank 0's step kernel: {bytes_launch} algorithmic bytes per launch "
+                             f"({'473' if model == 'tau1' else '521'} B per least-squares node update); "
+                             f"peak {pk_kind} burst copy"},
         "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cpu_threads, "kind": "oracle", "sample": cpu_desc},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 9 * 8 / e2e_steps,
-                "d2h_bytes_per_step": (n * 3 * 8 + 4 * 8 * len(CASES)) / e2e_steps,
-                "note": f"set_populations from pinned host memory + {e2e_steps} steps + get_fields + batch_drag_lift"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 3 * 8 / e2e_steps,
+                "d2h_bytes_per_step": (n * 3 * 8 + 8 * len(per_sample)) / e2e_steps,
+                "note": f"set_fields from pinned host memory + {e2e_steps} steps + get_fields + per-sample "
+                        f"{'permeability' if model == 'tau1' else 'drag'}, wall clock"},
         "gpu_launches": args.steps,
+        "setup_s": {"inputs": t_gen, "stencils": t_build, "tune_and_graphs": t_tune},
         "clocks": clk,
-        "cd_after_e2e": [round(float(v), 4) for v in forces["cd"]],
+        "per_sample_after_e2e": [round(v, 6) for v in per_sample][:8],
     }
+    if steady is not None:
+        out["time_to_steady"] = steady
     print(json.dumps(out))
 
 
@@ -313,10 +584,17 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="porous_batch", choices=["porous_batch", "karman_sweep"])
+    ap.add_argument("--samples", type=int, default=64, help="porous samples per batch (64: the configuration)")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"])
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed step kernel variant instead of the autotuner (-1: autotune)")
-    ap.add_argument("--node-order", default="hilbert", choices=ORDER_NAMES,
-                    help="node order used with --variant")
+    ap.add_argument("--node-order", default="hilbert", choices=ORDER_NAMES)
+    ap.add_argument("--tune-order", action="store_true", help="autotune the node order with the variant")
+    ap.add_argument("--no-steady", dest="steady", action="store_false", help="skip the time-to-steady legs")
+    ap.add_argument("--steady-samples", type=int, default=8)
+    ap.add_argument("--train-samples", type=int, default=32)
+    ap.add_argument("--train-nodes", type=int, default=100_000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

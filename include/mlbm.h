@@ -278,12 +278,56 @@ mlbm_status mlbm_permeability(mlbm_ctx* ctx, double* k, double* u_superficial, d
  * multiple of check; a ring of window / check FP32 velocity snapshots,
  * 8 bytes per node each, is allocated for the call when check < window and
  * must stay under 64 GB).  *steps_taken (may be NULL) receives the steps
- * advanced by this call.  Returns MLBM_E_DIVERGED on a non-finite velocity norm.
+ * advanced by this call.  At every evaluation (every `check` steps) the
+ * fluid nodes are also checked for divergence: a density that is not
+ * positive, or a non-finite density or velocity, returns MLBM_E_DIVERGED
+ * (the state is left as it is for inspection).
  */
 mlbm_status mlbm_run_to_steady(mlbm_ctx* ctx, double tol, int64_t window, int64_t max_steps,
                                int64_t* steps_taken);
 mlbm_status mlbm_run_to_steady_ex(mlbm_ctx* ctx, double tol, int64_t window, int64_t check, int64_t max_steps,
                                   int64_t* steps_taken);
+
+/*
+ * Step until the paper's steady-state criterion holds (Sec. 3.2, porous
+ * flow): with <u>(t) the superficial mean x-velocity, sum(u_x A) / box area
+ * (mlbm_permeability's u_superficial; Eq. (23)), recorded every `check`
+ * steps, and dn the paper's Delta n_t,
+ *   Delta u(t) = |<u>(t) - <u>(t - dn)| / (|<u>(t - dn)| dt dn)
+ * is evaluated every `check` steps from t = dn on (dn a multiple of check);
+ * the run is steady at the first t with Delta u < threshold (the paper uses
+ * threshold 1e-2, dn = 2e4).  A zero earlier mean is never steady.  dt is
+ * the physical time of one step; dt = 0 selects the paper's units (sample
+ * side length 1, kinematic viscosity 1): dt = nu (s / L)^2 with
+ * nu = (tau - 1/2)/3 and L the side of a square of the box's area, in the
+ * same length unit as s.  Divergence is checked as in mlbm_run_to_steady.
+ * *steps_taken (may be NULL) receives the steps advanced by this call.
+ * Single-sample contexts only (MLBM_E_INVALID otherwise; see
+ * mlbm_batch_run_to_steady_mean).  Errors: MLBM_E_INVALID (threshold <= 0,
+ * dn not a positive multiple of check, dt < 0), MLBM_E_DIVERGED,
+ * MLBM_E_NOT_CONVERGED, MLBM_E_CUDA, MLBM_E_TIMEOUT.
+ */
+mlbm_status mlbm_run_to_steady_mean(mlbm_ctx* ctx, double threshold, int64_t dn, int64_t check, double dt,
+                                    int64_t max_steps, int64_t* steps_taken);
+
+/*
+ * Bounded device waits.  The bulk-copy ring step variants (4..7) wait on
+ * shared-memory barriers for their tile copies; each wait gives up after
+ * `seconds` (default 2; accepted range [1e-4, 60]), records an error word,
+ * waits (bounded again) for the copies it issued and returns, and the next
+ * call that synchronises the context returns MLBM_E_TIMEOUT with the step's
+ * result invalid.  The context stays usable (reload a state with
+ * mlbm_set_populations / mlbm_set_fields).  No paper counterpart.
+ */
+mlbm_status mlbm_set_wait_limit(mlbm_ctx* ctx, double seconds);
+/*
+ * Test of the bounded waits: the next step launch (which must use a
+ * bulk-copy ring variant, 4..7, else MLBM_E_INVALID) issues no copies for
+ * the first tile of its first block, so that block's consumers wait for a
+ * tile that never arrives until the wait limit runs out.  One launch only;
+ * it is launched directly, never from a captured graph.  No paper counterpart.
+ */
+mlbm_status mlbm_test_withhold_copy(mlbm_ctx* ctx);
 
 /* Checkpoint the state, step count and parameters to a file / restore them
    into a context built from the same stencils (node count and K checked). */
@@ -398,6 +442,11 @@ mlbm_status mlbm_batch_run_to_steady(mlbm_ctx* ctx, double tol, int64_t window, 
                                      int64_t* steps_taken);
 mlbm_status mlbm_batch_run_to_steady_ex(mlbm_ctx* ctx, double tol, int64_t window, int64_t check,
                                         int64_t max_steps, int64_t* steps_taken);
+/* mlbm_run_to_steady_mean per sample (Sec. 3.2 criterion on each sample's
+   own <u>); dt[i] is sample i's physical time step (NULL: the paper's units
+   for every sample, as mlbm_run_to_steady_mean with dt = 0) */
+mlbm_status mlbm_batch_run_to_steady_mean(mlbm_ctx* ctx, double threshold, int64_t dn, int64_t check,
+                                          const double* dt, int64_t max_steps, int64_t* steps_taken);
 
 /*
  * Autotune the node order together with the kernel variant: for every
@@ -417,6 +466,63 @@ mlbm_status mlbm_autotune_order(mlbm_stencils* const* stencils, const mlbm_param
    starting buffer, re-captured when the variant or stream changes); enable = 0
    launches every step directly. */
 mlbm_status mlbm_set_graphs(mlbm_ctx* ctx, int enable);
+/* Capture and instantiate both step graphs (one per starting buffer) for the
+   context's current kernel variant and stream, without running a step, so
+   that a later timed mlbm_step replays graphs only.  No-op when graphs are
+   off.  Errors: MLBM_E_CUDA. */
+mlbm_status mlbm_prepare_graphs(mlbm_ctx* ctx);
+
+/* ------------------------------------------------------ partitioned step */
+/*
+ * A node set split into n_parts contiguous ranges of its device positions
+ * (the stencils' node order, Hilbert by default): partition q owns positions
+ * [bounds[q], bounds[q+1]) (bounds: n_parts + 1 entries, 0 first and the
+ * node count last, strictly increasing; NULL: equal counts).  The step of a
+ * node reads only its stencil members' post-collision states (Sec. 2.2,
+ * Eq. (12)), so each partition keeps, after its own nodes, halo slots for the
+ * members it references but does not own, grouped by owning partition.
+ *
+ * mlbm_partition_plan (host only, no device needed) describes the split:
+ * first[q], n_owned[q], n_halo[q] and halo_from[q * n_parts + o] (how many
+ * of q's halo nodes partition o owns); any output may be NULL.
+ * mlbm_partition_nodes lists partition `part`'s owned nodes (caller ids, in
+ * its local order) and its halo nodes (caller ids, in halo-slot order); either
+ * output may be NULL.  Errors: MLBM_E_INVALID (bad bounds or part).
+ */
+mlbm_status mlbm_partition_plan(const mlbm_stencils* st, int n_parts, const int64_t* bounds, int64_t* first,
+                                int64_t* n_owned, int64_t* n_halo, int64_t* halo_from);
+mlbm_status mlbm_partition_nodes(const mlbm_stencils* st, int n_parts, const int64_t* bounds, int part,
+                                 int64_t* owned_ids, int64_t* halo_ids);
+/*
+ * The partitioned step on the current device: one context per partition (its
+ * owned stencils and a state with halo slots), all on one stream.  Every
+ * mlbm_part_step advances each partition once, then for every pair (owner o,
+ * receiver q) packs o's new states of q's halo nodes into a buffer of o and
+ * copies it into q's own halo slots (cudaMemcpyAsync), so that no step reads
+ * another partition's memory; after n steps the stream is synchronised.
+ * A node's arithmetic is the unpartitioned context's, in the same order, so
+ * with the same kernel variant the results are bitwise equal to mlbm_init's.
+ * Fields and populations are in the caller's order for all nodes (as
+ * mlbm_set_fields / mlbm_get_populations); mlbm_part_permeability adds the
+ * partitions' FP64 sums in partition order.  mlbm_part_info gives a
+ * partition's first position, owned and halo counts and the bytes its halo
+ * receives per step.  Starts at rest.  No CUDA graphs.
+ * Errors: as mlbm_init, MLBM_E_INVALID for bad bounds.
+ */
+typedef struct mlbm_part mlbm_part;
+mlbm_status mlbm_part_init(mlbm_part** out, const mlbm_stencils* st, const mlbm_params* p, int n_parts,
+                           const int64_t* bounds);
+void mlbm_part_destroy(mlbm_part* part);
+mlbm_status mlbm_part_info(const mlbm_part* part, int q, int64_t* first, int64_t* n_owned, int64_t* n_halo,
+                           int64_t* halo_bytes_per_step);
+mlbm_status mlbm_part_set_kernel_variant(mlbm_part* part, int variant);
+mlbm_status mlbm_part_step(mlbm_part* part, int64_t n_steps);
+mlbm_status mlbm_part_set_fields(mlbm_part* part, const double* rho_u);
+mlbm_status mlbm_part_get_fields(mlbm_part* part, double* rho_u);
+mlbm_status mlbm_part_set_populations(mlbm_part* part, const double* f);
+mlbm_status mlbm_part_get_populations(mlbm_part* part, double* f);
+mlbm_status mlbm_part_permeability(mlbm_part* part, double* k, double* u_superficial, double* u_intrinsic,
+                                   double* tortuosity);
 
 /* ------------------------------------------------ device-level reductions */
 /*
@@ -428,6 +534,7 @@ mlbm_status mlbm_set_graphs(mlbm_ctx* ctx, int enable);
  * mlbm_reduce_scratch_doubles(n) entries), then one block adds the partials
  * in a fixed order, so the result is bitwise reproducible.  Asynchronous on
  * `stream` (a cudaStream_t, NULL = default stream).
+ * With n = 0 the sums are all zero and rho, ux, uy, area may be NULL.
  * Errors: MLBM_E_INVALID (null pointers, n < 0, scratch too small), MLBM_E_CUDA.
  */
 int64_t mlbm_reduce_scratch_doubles(int64_t n);
@@ -446,8 +553,11 @@ mlbm_status mlbm_reduce_fields_device(const float* rho, const float* ux, const f
  * reduction never needs more, for any n.  n must be in
  * [0, mlbm_reduce_noalloc_max_nodes()] (2^31 - 1), else MLBM_E_INVALID.
  * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  All calls share the array: calls that overlap
+ * device current (cudaGetSymbolAddress) and caches it for the current CUDA
+ * context; make that first call before any stream capture.  A call under a
+ * different context of the device (after cudaDeviceReset, or a context the
+ * caller made current) looks the address up again, so it is never taken from
+ * a context that is gone.  All calls share the array: calls that overlap
  * on the GPU (different streams, no ordering between them) race and give
  * wrong sums.  Nothing in it has to start at zero (each call writes every
  * partial it reads).  Calls no allocating routine.  Inputs and out[6] as for

@@ -27,6 +27,7 @@ struct mlbm_ctx {
     int device = 0;
     mlbm_params params{};
     int64_t n = 0, n_pad = 0;
+    int64_t n_halo = 0;  // state slots after the n nodes (partitions only)
     int K = 0;
     double s = 1.0, box_area = 1.0;
     cudaStream_t stream = nullptr;
@@ -78,6 +79,10 @@ struct mlbm_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_variant = -1;
     cudaStream_t graph_stream = nullptr;
+    // bounded waits of the bulk-copy ring variants (4..7): budget of one wait,
+    // and the test switch that makes the next launch withhold one tile
+    unsigned long long wait_ns = 2000000000ULL;
+    int withhold_next = 0;
 };
 
 namespace {
@@ -96,6 +101,18 @@ __global__ void l2_flush_read(const float4* __restrict__ buf, size_t n, float* s
         acc += (v.x + v.y) + (v.z + v.w);
     }
     if (acc != 0.f) *sink = acc;  // never taken on the zeroed buffer; keeps the loads
+}
+
+// Sending side of a halo copy: the states of the listed positions into one
+// contiguous block, w float4 per node (out[i*w + c] = in[list[i]*w + c]).
+__global__ void gather_states(const float4* __restrict__ in, const int* __restrict__ list, int64_t m, int w,
+                              float4* __restrict__ out) {
+    const int64_t total = m * w;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t node = i / w;
+        const int c = (int)(i - node * w);
+        out[i] = in[(size_t)list[node] * w + c];
+    }
 }
 
 namespace {
@@ -157,9 +174,12 @@ mlbm_status sync(mlbm_ctx* c) {
     MLBM_CUDA(cudaStreamSynchronize(c->stream));
     if (c->err) {
         int e = 0;
-        MLBM_CUDA(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+        MLBM_CUDA(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        MLBM_CUDA(cudaStreamSynchronize(c->stream));
         if (e != 0) {
-            MLBM_CUDA(cudaMemset(c->err, 0, sizeof(int)));
+            // cleared in stream order, before any later launch can set it again
+            MLBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+            MLBM_CUDA(cudaStreamSynchronize(c->stream));
             return set_error(MLBM_E_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(e) +
                                                  "); the step result is invalid");
         }
@@ -170,9 +190,12 @@ mlbm_status sync(mlbm_ctx* c) {
 mlbm_status launch_one_step(mlbm_ctx* c, int variant) {
     const int a = c->cur, b = c->cur ^ 1;
     const int model = c->params.model == MLBM_MODEL_BGK ? 0 : 1;
-    if (variant >= 4 && variant <= 7 && !c->S.Wr)
+    if (variant >= 4 && variant <= 7 && !c->S.Wr) {
+        const dev::Wait W{c->wait_ns, c->withhold_next};
+        c->withhold_next = 0;
         MLBM_CUDA(launch_step_tma(variant, model, c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->ruv[a], c->ruv[b],
-                                  c->C, c->err, c->stream));
+                                  c->C, c->err, W, c->stream));
+    }
     else if (model == 0)
         MLBM_CUDA(launch_bgk_step(c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->C, variant, c->stream));
     else
@@ -193,6 +216,9 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     c->box_area = H.box_area;
     c->n_pad = (H.n + 127) / 128 * 128;
     const int64_t n = H.n, np = c->n_pad;
+    // state slots: the nodes, then the halo copies of a partition's neighbours
+    c->n_halo = H.n_halo;
+    const int64_t nps = (H.n + H.n_halo + 127) / 128 * 128;
     const int K = H.K, Kq = K / 4;
     // ---- host-side device layout
     const bool rbf = H.interp == MLBM_INTERP_RBF;
@@ -219,8 +245,13 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
             // nearby addresses; the matrix columns follow the same order
             int order[32];
             for (int j = 0; j < K; ++j) order[j] = j;
-            std::sort(order, order + K,
-                      [&](int a, int b) { return H.idx[(size_t)q * K + a] < H.idx[(size_t)q * K + b]; });
+            if (H.slot_key.empty())
+                std::sort(order, order + K,
+                          [&](int a, int b) { return H.idx[(size_t)q * K + a] < H.idx[(size_t)q * K + b]; });
+            else
+                std::sort(order, order + K, [&](int a, int b) {
+                    return H.slot_key[(size_t)q * K + a] < H.slot_key[(size_t)q * K + b];
+                });
             for (int jj = 0; jj < K; ++jj) {
                 const int j = order[jj];
                 hidx[(((size_t)(jj / 4)) * np + q) * 4 + (jj % 4)] = H.idx[(size_t)q * K + j];
@@ -316,10 +347,10 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     MLBM_TRY(dalloc(c, &c->area_over_s2, np));
     for (int b = 0; b < 2; ++b) {
         if (p->model == MLBM_MODEL_BGK) {
-            MLBM_TRY(dalloc(c, &c->f8[b], (size_t)2 * np));
-            MLBM_TRY(dalloc(c, &c->f0[b], np));
+            MLBM_TRY(dalloc(c, &c->f8[b], (size_t)2 * nps));
+            MLBM_TRY(dalloc(c, &c->f0[b], nps));
         } else {
-            MLBM_TRY(dalloc(c, &c->ruv[b], np));
+            MLBM_TRY(dalloc(c, &c->ruv[b], nps));
         }
     }
     MLBM_TRY(dalloc(c, &c->rho, np));
@@ -357,10 +388,10 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     MLBM_CUDA(cudaMemsetAsync(c->py, 0, np * 4, c->stream));
     for (int b = 0; b < 2; ++b) {
         if (c->f8[b]) {
-            MLBM_CUDA(cudaMemsetAsync(c->f8[b], 0, (size_t)2 * np * sizeof(float4), c->stream));
-            MLBM_CUDA(cudaMemsetAsync(c->f0[b], 0, np * 4, c->stream));
+            MLBM_CUDA(cudaMemsetAsync(c->f8[b], 0, (size_t)2 * nps * sizeof(float4), c->stream));
+            MLBM_CUDA(cudaMemsetAsync(c->f0[b], 0, nps * 4, c->stream));
         }
-        if (c->ruv[b]) MLBM_CUDA(cudaMemsetAsync(c->ruv[b], 0, np * sizeof(float4), c->stream));
+        if (c->ruv[b]) MLBM_CUDA(cudaMemsetAsync(c->ruv[b], 0, nps * sizeof(float4), c->stream));
     }
     c->S.n = (int)n;
     c->S.n_pad = (int)np;
@@ -415,6 +446,43 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     return sync(c);
 }
 
+// instantiate the graph of kGraphSteps step launches that starts from buffer
+// `parity` (capture only: nothing runs, and the state is left as it was)
+mlbm_status ensure_graph(mlbm_ctx* c, int parity) {
+    cudaGraphExec_t& ex = c->graph[parity];
+    if (ex) return MLBM_OK;
+    const int saved = c->cur, saved_withhold = c->withhold_next;
+    c->cur = parity;
+    c->withhold_next = 0;  // never captured into a graph
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (ee != cudaSuccess) {
+        c->cur = saved;
+        c->withhold_next = saved_withhold;
+        return set_error(MLBM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+    }
+    mlbm_status cs = MLBM_OK;
+    for (int i = 0; i < kGraphSteps && cs == MLBM_OK; ++i) cs = launch_one_step(c, c->variant);
+    ee = cudaStreamEndCapture(c->stream, &g);
+    c->cur = saved;  // an even number of launches returns to it as well
+    c->withhold_next = saved_withhold;
+    if (cs != MLBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return cs;
+    }
+    if (ee != cudaSuccess) return set_error(MLBM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+    ee = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ee != cudaSuccess) {
+        ex = nullptr;
+        return set_error(MLBM_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
+    }
+    return MLBM_OK;
+}
+
+// graphs are tied to the variant and stream they were captured with
+void refresh_graphs(mlbm_ctx* c);
+
 void drop_graphs(mlbm_ctx* c) {
     for (int i = 0; i < 2; ++i)
         if (c->graph[i]) {
@@ -422,6 +490,14 @@ void drop_graphs(mlbm_ctx* c) {
             c->graph[i] = nullptr;
         }
     c->graph_variant = -1;
+}
+
+void refresh_graphs(mlbm_ctx* c) {
+    if (c->graph_variant != c->variant || c->graph_stream != c->stream) {
+        drop_graphs(c);
+        c->graph_variant = c->variant;
+        c->graph_stream = c->stream;
+    }
 }
 
 void free_ctx(mlbm_ctx* c) {
@@ -443,43 +519,94 @@ mlbm_status fields_to_work(mlbm_ctx* c, double* ru_dev_or_null) {
     return MLBM_OK;
 }
 
-// Steady-state iteration shared by the single and batched entry points: every
-// `check` steps each sample's velocity is compared with its own snapshot of
-// `window` steps earlier (a ring of window / check snapshots), delta =
-// |u(t) - u(t - window)|_2 / (window |u(t)|_2) over non-equilibrium nodes;
-// a sample is steady at the first t >= window with delta < tol.  at[i]
-// receives that t, or -1.  Steps stop once every sample is steady.
-mlbm_status run_steady(mlbm_ctx* c, double tol, int64_t window, int64_t check, int64_t max_steps, int64_t* at,
-                       const char* name) {
+// Steady-state iteration shared by the single and batched entry points.
+//
+// Criterion kFieldNorm (the build's own): every `check` steps each sample's
+// velocity is compared with its own snapshot of `window` steps earlier (a
+// ring of window / check snapshots), delta = |u(t) - u(t - window)|_2 /
+// (window |u(t)|_2) over non-equilibrium nodes; a sample is steady at the
+// first t >= window with delta < tol.
+//
+// Criterion kMeanVelocity (Sec. 3.2): every `check` steps the superficial
+// mean velocity <u>(t) = sum u_x A / box area of each sample is recorded; at
+// t >= window (the paper's Delta n_t) the relative rate
+//   Delta u = |<u>(t) - <u>(t - window)| / (|<u>(t - window)| dt window)
+// is formed with the sample's physical time step dt, and the sample is
+// steady at the first such t with Delta u < tol (the paper's threshold is
+// 1e-2 with Delta n_t = 2e4).  A zero earlier mean is never steady.
+//
+// Both criteria also check, at every snapshot, that each sample's density is
+// positive and its fields finite on every fluid node (MLBM_E_DIVERGED
+// otherwise).  at[i] receives the step of sample i's steady state, or -1.
+// Steps stop once every sample is steady.
+enum SteadyMode { kFieldNorm = 0, kMeanVelocity = 1 };
+
+mlbm_status run_steady(mlbm_ctx* c, int mode, double tol, int64_t window, int64_t check, int64_t max_steps,
+                       const double* dt, int64_t* at, const char* name) {
     const std::string nm(name);
     if (!(tol > 0) || window < 1 || check < 1 || window % check != 0 || max_steps < 0)
         return set_error(MLBM_E_INVALID, nm + ": bad arguments (window must be a positive multiple of check)");
     const int ns = (int)c->seg_off.size() - 1;
-    const int64_t R = window / check;
+    if (mode == kMeanVelocity && dt)
+        for (int i = 0; i < ns; ++i)
+            if (!(dt[i] > 0) || !std::isfinite(dt[i]))
+                return set_error(MLBM_E_INVALID, nm + ": time steps must be positive and finite");
+    const int64_t R = mode == kFieldNorm ? window / check : 1;
     const int64_t n = c->n;
     std::vector<int64_t> done_at(ns, -1);
     c->steps_in_last_run = 0;
     float* ring = nullptr;
+    double* means = nullptr;
     if (R > 1) {
         if ((double)R * 2.0 * (double)n * 4.0 > 64e9)
             return set_error(MLBM_E_INVALID, nm + ": snapshot ring over 64 GB (use a larger check interval)");
         MLBM_CUDA(cudaMallocAsync(&ring, (size_t)R * 2 * (size_t)n * sizeof(float), c->stream));
     }
+    if (mode == kMeanVelocity) {
+        cudaError_t e = cudaMallocAsync(&means, 48 * (size_t)ns, c->stream);
+        if (e != cudaSuccess) {
+            if (ring) cudaFreeAsync(ring, c->stream);
+            cudaStreamSynchronize(c->stream);
+            return set_error(MLBM_E_OOM, nm + ": " + cudaGetErrorString(e));
+        }
+    }
     auto slot_u = [&](int64_t k) { return R > 1 ? ring + (size_t)k * 2 * n : c->px; };
     auto slot_v = [&](int64_t k) { return R > 1 ? ring + ((size_t)k * 2 + 1) * n : c->py; };
-    std::vector<double> h(2 * (size_t)ns);
-    auto snapshot = [&](int64_t k, bool read) -> mlbm_status {
+    std::vector<double> h(3 * (size_t)ns), hm(6 * (size_t)ns);
+    std::vector<std::vector<double>> hist(ns);  // <u> every `check` steps (mean-velocity criterion)
+    // physical time step of each sample: the caller's, else the paper's
+    // units (side length 1, kinematic viscosity 1): dt = nu_lb (s / L)^2 with
+    // L the side of a square of the sample's box area
+    std::vector<double> dts(ns, 1.0);
+    for (int i = 0; i < ns; ++i) {
+        const double si = c->seg_s.empty() ? c->s : c->seg_s[i];
+        const double L = std::sqrt(c->seg_box_area[i]);
+        dts[i] = dt ? dt[i] : (c->seg_params[i].tau - 0.5) / 3.0 * (si / L) * (si / L);
+    }
+    auto snapshot = [&](int64_t k) -> mlbm_status {
         MLBM_TRY(fields_to_work(c, nullptr));
         for (int i = 0; i < ns; ++i) {
             const int64_t o = c->seg_off[i], m = c->seg_off[i + 1] - o;
-            MLBM_CUDA(launch_change(c->ux + o, c->uy + o, slot_u(k) + o, slot_v(k) + o, c->mask + o, m, c->scratch,
-                                    c->seg_out + 2 * i, c->stream));
+            MLBM_CUDA(launch_change(c->rho + o, c->ux + o, c->uy + o, slot_u(k) + o, slot_v(k) + o, c->mask + o, m,
+                                    c->scratch, c->seg_out + 3 * i, c->stream));
+            if (means)
+                MLBM_CUDA(launch_reduce_fields(c->rho + o, c->ux + o, c->uy + o, c->area + o, c->mask + o, m,
+                                               c->scratch, means + 6 * i, c->stream));
         }
-        if (read) MLBM_CUDA(cudaMemcpyAsync(h.data(), c->seg_out, 16 * (size_t)ns, cudaMemcpyDeviceToHost, c->stream));
-        return sync(c);
+        MLBM_CUDA(cudaMemcpyAsync(h.data(), c->seg_out, 24 * (size_t)ns, cudaMemcpyDeviceToHost, c->stream));
+        if (means) MLBM_CUDA(cudaMemcpyAsync(hm.data(), means, 48 * (size_t)ns, cudaMemcpyDeviceToHost, c->stream));
+        MLBM_TRY(sync(c));
+        for (int i = 0; i < ns; ++i) {
+            if (h[3 * i + 2] != 0.0 || !std::isfinite(h[3 * i]) || !std::isfinite(h[3 * i + 1]))
+                return set_error(MLBM_E_DIVERGED, nm + ": non-positive density or non-finite field in sample " +
+                                                      std::to_string(i) + " (" +
+                                                      std::to_string((int64_t)h[3 * i + 2]) + " nodes)");
+            if (means) hist[i].push_back(hm[6 * i + 2] / c->seg_box_area[i]);
+        }
+        return MLBM_OK;
     };
     auto body = [&]() -> mlbm_status {
-        MLBM_TRY(snapshot(0, false));
+        MLBM_TRY(snapshot(0));
         int64_t t = 0;
         int remaining = ns;
         while (t < max_steps && remaining > 0) {
@@ -488,15 +615,20 @@ mlbm_status run_steady(mlbm_ctx* c, double tol, int64_t window, int64_t check, i
             t += w;
             c->steps_in_last_run = t;
             if (w != check) break;  // a partial chunk at max_steps is not evaluated
-            const bool eval = t >= window;
-            MLBM_TRY(snapshot((t / check) % R, eval));
-            if (!eval) continue;
+            MLBM_TRY(snapshot((t / check) % R));
+            if (t < window) continue;
             for (int i = 0; i < ns; ++i) {
                 if (done_at[i] >= 0) continue;
-                if (!std::isfinite(h[2 * i]) || !std::isfinite(h[2 * i + 1]))
-                    return set_error(MLBM_E_DIVERGED, nm + ": non-finite velocity in sample " + std::to_string(i));
-                const double delta = h[2 * i + 1] > 0 ? std::sqrt(h[2 * i] / h[2 * i + 1]) / (double)window : 0.0;
-                if (delta < tol) {
+                bool steady;
+                if (mode == kFieldNorm) {
+                    const double delta = h[3 * i + 1] > 0 ? std::sqrt(h[3 * i] / h[3 * i + 1]) / (double)window : 0.0;
+                    steady = delta < tol;
+                } else {
+                    const size_t j = hist[i].size() - 1, lag = (size_t)(window / check);
+                    const double now = hist[i][j], then = hist[i][j - lag];
+                    steady = then != 0.0 && std::fabs(now - then) / (std::fabs(then) * dts[i] * (double)window) < tol;
+                }
+                if (steady) {
                     done_at[i] = t;
                     --remaining;
                 }
@@ -505,10 +637,9 @@ mlbm_status run_steady(mlbm_ctx* c, double tol, int64_t window, int64_t check, i
         return remaining == 0 ? MLBM_OK : set_error(MLBM_E_NOT_CONVERGED, nm + ": max_steps reached");
     };
     mlbm_status st = body();
-    if (ring) {
-        cudaFreeAsync(ring, c->stream);
-        cudaStreamSynchronize(c->stream);
-    }
+    if (ring) cudaFreeAsync(ring, c->stream);
+    if (means) cudaFreeAsync(means, c->stream);
+    if (ring || means) cudaStreamSynchronize(c->stream);
     if (at)
         for (int i = 0; i < ns; ++i) at[i] = done_at[i];
     return st;
@@ -597,34 +728,12 @@ mlbm_status mlbm_step(mlbm_ctx* c, int64_t n_steps) {
     if (n_steps == 0) return MLBM_OK;
     if (c->timing) MLBM_CUDA(cudaEventRecord(c->ev0, c->stream));
     int64_t left = n_steps;
-    if (c->use_graphs && n_steps >= kGraphSteps) {
-        if (c->graph_variant != c->variant || c->graph_stream != c->stream) {
-            drop_graphs(c);
-            c->graph_variant = c->variant;
-            c->graph_stream = c->stream;
-        }
+    // a launch that must withhold a tile runs directly, not from a graph
+    if (c->use_graphs && n_steps >= kGraphSteps && !c->withhold_next) {
+        refresh_graphs(c);
         while (left >= kGraphSteps) {
-            cudaGraphExec_t& ex = c->graph[c->cur];
-            if (!ex) {
-                // capture kGraphSteps launches; cur returns to its value (even count)
-                cudaGraph_t g = nullptr;
-                MLBM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-                mlbm_status cs = MLBM_OK;
-                for (int i = 0; i < kGraphSteps && cs == MLBM_OK; ++i) cs = launch_one_step(c, c->variant);
-                cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
-                if (cs != MLBM_OK) {
-                    if (g) cudaGraphDestroy(g);
-                    return cs;
-                }
-                if (ee != cudaSuccess) return set_error(MLBM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
-                ee = cudaGraphInstantiate(&ex, g, 0);
-                cudaGraphDestroy(g);
-                if (ee != cudaSuccess) {
-                    ex = nullptr;
-                    return set_error(MLBM_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
-                }
-            }
-            MLBM_CUDA(cudaGraphLaunch(ex, c->stream));
+            MLBM_TRY(ensure_graph(c, c->cur));
+            MLBM_CUDA(cudaGraphLaunch(c->graph[c->cur], c->stream));
             left -= kGraphSteps;
         }
     }
@@ -637,6 +746,32 @@ mlbm_status mlbm_step(mlbm_ctx* c, int64_t n_steps) {
         MLBM_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
         c->last_ms = ms / (double)n_steps;
     }
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_prepare_graphs(mlbm_ctx* c) {
+    if (!c) return set_error(MLBM_E_INVALID, "prepare_graphs: NULL context");
+    if (!c->use_graphs) return MLBM_OK;
+    refresh_graphs(c);
+    MLBM_TRY(ensure_graph(c, 0));
+    MLBM_TRY(ensure_graph(c, 1));
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_set_wait_limit(mlbm_ctx* c, double seconds) {
+    if (!c) return set_error(MLBM_E_INVALID, "set_wait_limit: NULL context");
+    if (!(seconds >= 1e-4 && seconds <= 60.0))
+        return set_error(MLBM_E_INVALID, "set_wait_limit: the limit must lie in [1e-4, 60] seconds");
+    c->wait_ns = (unsigned long long)(seconds * 1e9);
+    drop_graphs(c);  // captured launches carry the old limit
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_test_withhold_copy(mlbm_ctx* c) {
+    if (!c) return set_error(MLBM_E_INVALID, "test_withhold_copy: NULL context");
+    if (c->variant < 4 || c->variant > 7 || c->S.Wr)
+        return set_error(MLBM_E_INVALID, "test_withhold_copy: the context's kernel variant has no bulk-copy ring");
+    c->withhold_next = 1;
     return MLBM_OK;
 }
 
@@ -764,7 +899,20 @@ mlbm_status mlbm_run_to_steady_ex(mlbm_ctx* c, double tol, int64_t window, int64
     if (!c) return set_error(MLBM_E_INVALID, "run_to_steady: NULL context");
     if (taken) *taken = 0;
     int64_t at = -1;
-    mlbm_status st = run_steady(c, tol, window, check, max_steps, &at, "run_to_steady");
+    mlbm_status st = run_steady(c, kFieldNorm, tol, window, check, max_steps, nullptr, &at, "run_to_steady");
+    if (taken) *taken = at >= 0 ? at : c->steps_in_last_run;
+    return st;
+}
+
+mlbm_status mlbm_run_to_steady_mean(mlbm_ctx* c, double threshold, int64_t dn, int64_t check, double dt,
+                                    int64_t max_steps, int64_t* taken) {
+    if (!c) return set_error(MLBM_E_INVALID, "run_to_steady_mean: NULL context");
+    if (taken) *taken = 0;
+    if (c->seg_off.size() != 2) return set_error(MLBM_E_INVALID, "run_to_steady_mean: batched context");
+    int64_t at = -1;
+    const double* dtp = dt > 0 ? &dt : nullptr;
+    if (dt < 0 || !std::isfinite(dt)) return set_error(MLBM_E_INVALID, "run_to_steady_mean: bad time step");
+    mlbm_status st = run_steady(c, kMeanVelocity, threshold, dn, check, max_steps, dtp, &at, "run_to_steady_mean");
     if (taken) *taken = at >= 0 ? at : c->steps_in_last_run;
     return st;
 }
@@ -1107,7 +1255,13 @@ mlbm_status mlbm_batch_run_to_steady(mlbm_ctx* c, double tol, int64_t window, in
 mlbm_status mlbm_batch_run_to_steady_ex(mlbm_ctx* c, double tol, int64_t window, int64_t check, int64_t max_steps,
                                         int64_t* taken) {
     if (!c) return set_error(MLBM_E_INVALID, "batch_run_to_steady: NULL context");
-    return run_steady(c, tol, window, check, max_steps, taken, "batch_run_to_steady");
+    return run_steady(c, kFieldNorm, tol, window, check, max_steps, nullptr, taken, "batch_run_to_steady");
+}
+
+mlbm_status mlbm_batch_run_to_steady_mean(mlbm_ctx* c, double threshold, int64_t dn, int64_t check,
+                                          const double* dt, int64_t max_steps, int64_t* taken) {
+    if (!c) return set_error(MLBM_E_INVALID, "batch_run_to_steady_mean: NULL context");
+    return run_steady(c, kMeanVelocity, threshold, dn, check, max_steps, dt, taken, "batch_run_to_steady_mean");
 }
 
 mlbm_status mlbm_batch_drag_lift(mlbm_ctx* c, const double* ref_length, const double* u_ref, double* fx, double* fy,
@@ -1271,11 +1425,258 @@ mlbm_status mlbm_reduce_fields_device(const float* rho, const float* ux, const f
                                       const uint8_t* mask, int64_t n, double* scratch, int64_t scratch_len,
                                       double* out, void* stream) {
     clear_error();
-    if (!rho || !ux || !uy || !area || !scratch || !out || n < 0)
+    // the node arrays may be NULL when there are no nodes
+    if ((n > 0 && (!rho || !ux || !uy || !area)) || !scratch || !out || n < 0)
         return set_error(MLBM_E_INVALID, "reduce_fields_device: NULL pointer or negative n");
     if (scratch_len < mlbm_reduce_scratch_doubles(n))
         return set_error(MLBM_E_INVALID, "reduce_fields_device: scratch too small");
     MLBM_CUDA(launch_reduce_fields(rho, ux, uy, area, mask, n, scratch, out, static_cast<cudaStream_t>(stream)));
+    return MLBM_OK;
+}
+
+// ------------------------------------------------------ partitioned step
+// P logical partitions of one node set, each a context over a contiguous
+// range of the device positions with halo slots after its own nodes.  After
+// every step each partition's new states of the nodes that another
+// partition references are packed (on the owner) and copied into that
+// partition's own halo slots, so every step reads local memory only.  All
+// partitions live on the current device and run on one stream, in order.
+}  // extern "C"
+
+struct mlbm_part {
+    int P = 0;
+    int model = 0;
+    double box_area = 1.0;
+    std::vector<mlbm_ctx*> ctx;
+    std::vector<std::vector<int64_t>> caller_ids;  // [P][n_owned]: the caller's node id of each local position
+    std::vector<int64_t> first, n_owned, n_halo;
+    struct Block {
+        int q, o;           // receiver, owner
+        int64_t count;      // nodes
+        int64_t halo_off;   // first halo slot of the block in q
+        int* list;          // device: positions local to o
+        float4* buf;        // device: packed states
+    };
+    std::vector<Block> blocks;
+    cudaStream_t stream = nullptr;
+    std::vector<void*> allocations;
+    int64_t steps = 0;
+};
+
+namespace {
+
+void free_part(mlbm_part* P) {
+    if (!P) return;
+    if (P->stream) cudaStreamSynchronize(P->stream);
+    for (mlbm_ctx* c : P->ctx) free_ctx(c);
+    for (void* q : P->allocations) cudaFree(q);
+    if (P->stream) cudaStreamDestroy(P->stream);
+    delete P;
+}
+
+int state_width(const mlbm_part* P) { return P->model == MLBM_MODEL_BGK ? 2 : 1; }
+
+float4* state_of(mlbm_ctx* c) { return c->f8[c->cur] ? c->f8[c->cur] : c->ruv[c->cur]; }
+
+// fill every partition's halo slots from the owners' current states
+mlbm_status exchange(mlbm_part* P) {
+    const int w = state_width(P);
+    for (const mlbm_part::Block& b : P->blocks) {
+        const int grid = (int)std::min<int64_t>(4 * 152, (b.count * w + 255) / 256);
+        gather_states<<<std::max(grid, 1), 256, 0, P->stream>>>(state_of(P->ctx[b.o]), b.list, b.count, w, b.buf);
+        MLBM_CUDA(cudaGetLastError());
+        float4* dst = state_of(P->ctx[b.q]) + (size_t)(P->n_owned[b.q] + b.halo_off) * w;
+        MLBM_CUDA(cudaMemcpyAsync(dst, b.buf, (size_t)b.count * w * sizeof(float4), cudaMemcpyDeviceToDevice,
+                                  P->stream));
+    }
+    return MLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mlbm_status mlbm_part_init(mlbm_part** out, const mlbm_stencils* st, const mlbm_params* p, int n_parts,
+                           const int64_t* bounds) {
+    clear_error();
+    if (!out || !st || !p) return set_error(MLBM_E_INVALID, "part_init: NULL argument");
+    *out = nullptr;
+    MLBM_TRY(check_params(p));
+    if (st->h.n > (int64_t(1) << 31) - 1) return set_error(MLBM_E_INVALID, "part_init: too many nodes");
+    PartPlan plan;
+    MLBM_TRY(make_part_plan(st->h, n_parts, bounds, plan));
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        (void)cudaGetLastError();
+        return set_error(MLBM_E_CUDA, "part_init: no CUDA device");
+    }
+    auto* P = new (std::nothrow) mlbm_part;
+    if (!P) return set_error(MLBM_E_OOM, "part_init: out of host memory");
+    P->P = n_parts;
+    P->model = p->model;
+    P->box_area = st->h.box_area;
+    auto fail = [&](mlbm_status s) {
+        std::string msg = g_last_error;
+        free_part(P);
+        return set_error(s, msg);
+    };
+    if (cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(set_error(MLBM_E_CUDA, "part_init: stream"));
+    for (int q = 0; q < n_parts; ++q) {
+        auto* sub = new (std::nothrow) mlbm_stencils;
+        if (!sub) return fail(set_error(MLBM_E_OOM, "part_init: out of host memory"));
+        sub->h = slice_partition(st->h, plan, q);
+        auto* c = new (std::nothrow) mlbm_ctx;
+        if (!c) {
+            delete sub;
+            return fail(set_error(MLBM_E_OOM, "part_init: out of host memory"));
+        }
+        P->ctx.push_back(c);
+        mlbm_status s = do_init(c, sub, p, nullptr, nullptr);
+        delete sub;
+        if (s != MLBM_OK) return fail(s);
+        c->stream = P->stream;
+        c->use_graphs = false;
+        const int64_t a = plan.bounds[q], e = plan.bounds[q + 1];
+        P->first.push_back(a);
+        P->n_owned.push_back(e - a);
+        P->n_halo.push_back((int64_t)plan.halo[q].size());
+        P->caller_ids.emplace_back(st->h.perm.begin() + a, st->h.perm.begin() + e);
+    }
+    const int w = p->model == MLBM_MODEL_BGK ? 2 : 1;
+    for (int q = 0; q < n_parts; ++q)
+        for (int o = 0; o < n_parts; ++o) {
+            const int64_t h0 = plan.halo_off[q][o], h1 = plan.halo_off[q][o + 1];
+            if (h1 == h0) continue;
+            std::vector<int> list((size_t)(h1 - h0));
+            for (int64_t i = h0; i < h1; ++i) list[(size_t)(i - h0)] = (int)(plan.halo[q][(size_t)i] - plan.bounds[o]);
+            mlbm_part::Block b{q, o, h1 - h0, h0, nullptr, nullptr};
+            void* d = nullptr;
+            if (cudaMalloc(&d, list.size() * sizeof(int)) != cudaSuccess)
+                return fail(set_error(MLBM_E_OOM, "part_init: cudaMalloc"));
+            P->allocations.push_back(d);
+            b.list = static_cast<int*>(d);
+            if (cudaMalloc(&d, (size_t)b.count * w * sizeof(float4)) != cudaSuccess)
+                return fail(set_error(MLBM_E_OOM, "part_init: cudaMalloc"));
+            P->allocations.push_back(d);
+            b.buf = static_cast<float4*>(d);
+            if (cudaMemcpyAsync(b.list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, P->stream) !=
+                cudaSuccess)
+                return fail(set_error(MLBM_E_CUDA, "part_init: upload"));
+            if (cudaStreamSynchronize(P->stream) != cudaSuccess)
+                return fail(set_error(MLBM_E_CUDA, "part_init: upload"));
+            P->blocks.push_back(b);
+        }
+    mlbm_status s = exchange(P);
+    if (s == MLBM_OK) s = sync(P->ctx[0]);
+    if (s != MLBM_OK) return fail(s);
+    *out = P;
+    return MLBM_OK;
+}
+
+void mlbm_part_destroy(mlbm_part* P) { free_part(P); }
+
+mlbm_status mlbm_part_info(const mlbm_part* P, int part, int64_t* first, int64_t* n_owned, int64_t* n_halo,
+                           int64_t* halo_bytes_per_step) {
+    if (!P || part < 0 || part >= P->P) return set_error(MLBM_E_INVALID, "part_info: bad argument");
+    if (first) *first = P->first[part];
+    if (n_owned) *n_owned = P->n_owned[part];
+    if (n_halo) *n_halo = P->n_halo[part];
+    if (halo_bytes_per_step) *halo_bytes_per_step = P->n_halo[part] * state_width(P) * (int64_t)sizeof(float4);
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_part_set_kernel_variant(mlbm_part* P, int variant) {
+    if (!P) return set_error(MLBM_E_INVALID, "part_set_kernel_variant: NULL");
+    for (mlbm_ctx* c : P->ctx) MLBM_TRY(mlbm_set_kernel_variant(c, variant));
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_part_step(mlbm_part* P, int64_t n_steps) {
+    if (!P) return set_error(MLBM_E_INVALID, "part_step: NULL");
+    if (n_steps < 0) return set_error(MLBM_E_INVALID, "part_step: negative step count");
+    for (int64_t t = 0; t < n_steps; ++t) {
+        for (mlbm_ctx* c : P->ctx) {
+            MLBM_TRY(launch_one_step(c, c->variant));
+            ++c->steps;
+        }
+        MLBM_TRY(exchange(P));
+        ++P->steps;
+    }
+    for (mlbm_ctx* c : P->ctx) MLBM_TRY(sync(c));  // also reports a bounded wait that ran out
+    return MLBM_OK;
+}
+
+// fields or populations in the caller's order for all nodes; `width` values per node
+static mlbm_status part_set(mlbm_part* P, const double* v, int width, bool fields) {
+    std::vector<double> loc;
+    for (int q = 0; q < P->P; ++q) {
+        const std::vector<int64_t>& ids = P->caller_ids[q];
+        loc.assign(ids.size() * width, 0.0);
+        for (size_t p = 0; p < ids.size(); ++p)
+            for (int k = 0; k < width; ++k) loc[p * width + k] = v[(size_t)ids[p] * width + k];
+        MLBM_TRY(fields ? mlbm_set_fields(P->ctx[q], loc.data()) : mlbm_set_populations(P->ctx[q], loc.data()));
+    }
+    MLBM_TRY(exchange(P));
+    P->steps = 0;
+    return sync(P->ctx[0]);
+}
+
+static mlbm_status part_get(mlbm_part* P, double* v, int width, bool fields) {
+    std::vector<double> loc;
+    for (int q = 0; q < P->P; ++q) {
+        const std::vector<int64_t>& ids = P->caller_ids[q];
+        loc.assign(ids.size() * width, 0.0);
+        MLBM_TRY(fields ? mlbm_get_fields(P->ctx[q], loc.data()) : mlbm_get_populations(P->ctx[q], loc.data()));
+        for (size_t p = 0; p < ids.size(); ++p)
+            for (int k = 0; k < width; ++k) v[(size_t)ids[p] * width + k] = loc[p * width + k];
+    }
+    return MLBM_OK;
+}
+
+mlbm_status mlbm_part_set_fields(mlbm_part* P, const double* ru) {
+    if (!P || !ru) return set_error(MLBM_E_INVALID, "part_set_fields: NULL argument");
+    return part_set(P, ru, 3, true);
+}
+
+mlbm_status mlbm_part_get_fields(mlbm_part* P, double* ru) {
+    if (!P || !ru) return set_error(MLBM_E_INVALID, "part_get_fields: NULL argument");
+    return part_get(P, ru, 3, true);
+}
+
+mlbm_status mlbm_part_set_populations(mlbm_part* P, const double* f) {
+    if (!P || !f) return set_error(MLBM_E_INVALID, "part_set_populations: NULL argument");
+    if (P->model != MLBM_MODEL_BGK) return set_error(MLBM_E_INVALID, "part_set_populations: BGK only");
+    return part_set(P, f, 9, false);
+}
+
+mlbm_status mlbm_part_get_populations(mlbm_part* P, double* f) {
+    if (!P || !f) return set_error(MLBM_E_INVALID, "part_get_populations: NULL argument");
+    if (P->model != MLBM_MODEL_BGK) return set_error(MLBM_E_INVALID, "part_get_populations: BGK only");
+    return part_get(P, f, 9, false);
+}
+
+mlbm_status mlbm_part_permeability(mlbm_part* P, double* k, double* us, double* ui, double* tort) {
+    if (!P) return set_error(MLBM_E_INVALID, "part_permeability: NULL");
+    // each partition's six FP64 sums, then added in partition order (the
+    // all-reduce of a run whose partitions live on separate devices)
+    double tot[6] = {0, 0, 0, 0, 0, 0};
+    for (mlbm_ctx* c : P->ctx) {
+        MLBM_TRY(fields_to_work(c, nullptr));
+        MLBM_CUDA(launch_reduce_fields(c->rho, c->ux, c->uy, c->area, c->mask, c->n, c->scratch, c->small, c->stream));
+        double h[6];
+        MLBM_CUDA(cudaMemcpyAsync(h, c->small, 48, cudaMemcpyDeviceToHost, c->stream));
+        MLBM_TRY(sync(c));
+        for (int i = 0; i < 6; ++i) tot[i] += h[i];
+    }
+    const mlbm_params& pp = P->ctx[0]->params;
+    const double sup = tot[2] / P->box_area;
+    const double gmag = std::sqrt(pp.gx * pp.gx + pp.gy * pp.gy);
+    const double nu = (pp.tau - 0.5) / 3.0;
+    if (us) *us = sup;
+    if (ui) *ui = tot[0] != 0 ? tot[2] / tot[0] : 0.0;
+    if (k) *k = gmag > 0 ? nu * sup / gmag : 0.0;
+    if (tort) *tort = tot[2] != 0 ? tot[4] / tot[2] : 0.0;
     return MLBM_OK;
 }
 

@@ -67,6 +67,13 @@ struct Stencil {
     int stage_max;
 };
 
+// bounded waits of the bulk-copy ring kernels: time budget of one wait, and a
+// test switch that makes block 0 withhold its first tile's copies
+struct Wait {
+    unsigned long long budget_ns;
+    int withhold;
+};
+
 constexpr int kStageTile = 256;   // nodes per staged tile (one block)
 constexpr int kStageMax = 1536;   // largest neighbourhood that is staged (48 KiB per buffer)
 

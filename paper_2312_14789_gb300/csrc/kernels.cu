@@ -1242,16 +1242,21 @@ __global__ void __launch_bounds__(kRedThreads) reduce_fields_final(int nb, const
     if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// sum |u - u_prev|^2, sum |u|^2 over masked nodes, then copy u into u_prev
-__global__ void __launch_bounds__(kRedThreads) change_partial(int64_t n, const float* __restrict__ ux,
+// over masked nodes: sum |u - u_prev|^2, sum |u|^2, and the number of nodes
+// whose density is not positive or whose fields are not finite; then copy u
+// into u_prev
+__global__ void __launch_bounds__(kRedThreads) change_partial(int64_t n, const float* __restrict__ rho,
+                                                               const float* __restrict__ ux,
                                                                const float* __restrict__ uy,
                                                                float* __restrict__ px, float* __restrict__ py,
                                                                const uint8_t* __restrict__ mask,
                                                                double* __restrict__ partial) {
-    double d = 0, m = 0;
+    double d = 0, m = 0, bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float u = ux[i], v = uy[i];
         if (!mask || mask[i]) {
+            const float r = rho[i];
+            if (!(r > 0.f) || !isfinite(r) || !isfinite(u) || !isfinite(v)) bad += 1.0;
             const double du = (double)u - px[i], dv = (double)v - py[i];
             d += du * du + dv * dv;
             m += (double)u * u + (double)v * v;
@@ -1259,20 +1264,37 @@ __global__ void __launch_bounds__(kRedThreads) change_partial(int64_t n, const f
         px[i] = u;
         py[i] = v;
     }
-    __shared__ double sd[kRedThreads], sm[kRedThreads];
+    __shared__ double sd[kRedThreads], sm[kRedThreads], sb[kRedThreads];
     sd[threadIdx.x] = d;
     sm[threadIdx.x] = m;
+    sb[threadIdx.x] = bad;
     __syncthreads();
     for (int h = kRedThreads / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) {
             sd[threadIdx.x] += sd[threadIdx.x + h];
             sm[threadIdx.x] += sm[threadIdx.x + h];
+            sb[threadIdx.x] += sb[threadIdx.x + h];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        partial[2 * (size_t)blockIdx.x] = sd[0];
-        partial[2 * (size_t)blockIdx.x + 1] = sm[0];
+        partial[3 * (size_t)blockIdx.x] = sd[0];
+        partial[3 * (size_t)blockIdx.x + 1] = sm[0];
+        partial[3 * (size_t)blockIdx.x + 2] = sb[0];
+    }
+}
+
+__global__ void sum_triples(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int i = 0; i < nb; ++i) {
+            a += partial[3 * i];
+            b += partial[3 * i + 1];
+            c += partial[3 * i + 2];
+        }
+        out[0] = a;
+        out[1] = b;
+        out[2] = c;
     }
 }
 
@@ -1527,11 +1549,11 @@ cudaError_t launch_reduce_fields(const float* rho, const float* ux, const float*
     return cudaGetLastError();
 }
 
-cudaError_t launch_change(const float* ux, const float* uy, float* px, float* py, const uint8_t* mask, int64_t n,
-                          double* partial, double* out, cudaStream_t st) {
+cudaError_t launch_change(const float* rho, const float* ux, const float* uy, float* px, float* py,
+                          const uint8_t* mask, int64_t n, double* partial, double* out, cudaStream_t st) {
     const int nb = reduce_blocks(n);
-    dev::change_partial<<<nb, dev::kRedThreads, 0, st>>>(n, ux, uy, px, py, mask, partial);
-    dev::sum_pairs<<<1, 32, 0, st>>>(nb, partial, out);
+    dev::change_partial<<<nb, dev::kRedThreads, 0, st>>>(n, rho, ux, uy, px, py, mask, partial);
+    dev::sum_triples<<<1, 32, 0, st>>>(nb, partial, out);
     return cudaGetLastError();
 }
 

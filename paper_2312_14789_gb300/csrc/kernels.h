@@ -34,7 +34,7 @@ cudaError_t launch_macroscopics(int model, int n, const int* perm, const float4*
 bool tma_supported(int Kq);
 cudaError_t launch_step_tma(int variant, int model, const dev::Stencil& S, const float4* f8in, const float* f0in,
                             float4* f8out, float* f0out, const float4* rin, float4* rout, const dev::Collide& C,
-                            int* err, cudaStream_t st);
+                            int* err, const dev::Wait& W, cudaStream_t st);
 int force_blocks(int n_link_nodes);
 cudaError_t launch_force(const dev::Stencil& S, int model, int n_link_nodes, const int* link_nodes,
                          const float* area_over_s2, const float4* f8, const float4* ruv, const dev::Collide& C,
@@ -44,8 +44,10 @@ constexpr int kReduceMaxBlocks = 1024;
 int reduce_blocks(int64_t n);
 cudaError_t launch_reduce_fields(const float* rho, const float* ux, const float* uy, const float* area,
                                  const uint8_t* mask, int64_t n, double* partial, double* out, cudaStream_t st);
-cudaError_t launch_change(const float* ux, const float* uy, float* px, float* py, const uint8_t* mask, int64_t n,
-                          double* partial, double* out, cudaStream_t st);
+// per sample: sum |u - u_prev|^2, sum |u|^2 and the count of nodes with a
+// non-positive density or non-finite field (3 doubles into out); u -> u_prev
+cudaError_t launch_change(const float* rho, const float* ux, const float* uy, float* px, float* py,
+                          const uint8_t* mask, int64_t n, double* partial, double* out, cudaStream_t st);
 
 // warm start (features.cu)
 cudaError_t launch_warm_check(int n, const int* perm, const uint16_t* node_sample, const uint8_t* meta,

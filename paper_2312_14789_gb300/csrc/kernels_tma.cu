@@ -12,9 +12,14 @@
 // as many CTAs as fit on the SMs; each walks the tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...
 //
-// Every mbarrier wait is bounded (clock64 budget of about two seconds); a wait
-// that runs out records an error code in *err and the thread leaves the loop,
-// so a lost copy cannot hang the GPU.  The host reads *err after the run.
+// Every mbarrier wait is bounded by a time budget (nanoseconds of the global
+// timer, two seconds unless the context sets another); a wait that runs out
+// records an error code in *err and the warp leaves the loop, so a lost copy
+// cannot hang the GPU.  The producer then waits (bounded again) for every
+// copy it issued that may still be landing before the CTA exits.  The host
+// reads *err after the run.  For tests of that path the host can ask one
+// launch to withhold the copies of block 0's first tile, so that the
+// consumers' wait for it runs out (Wait::withhold).
 #include <cstdio>
 
 #include "device_common.cuh"
@@ -43,12 +48,18 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* b, uint32_t parity) 
         : "memory");
     return ok;
 }
-// wait for the phase of the given parity to complete; false after ~budget cycles
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long budget) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for the phase of the given parity to complete; false once budget_ns
+// nanoseconds have passed without it
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, unsigned long long budget_ns) {
     if (mbar_try_wait(b, parity)) return true;
-    const long long t0 = clock64();
+    const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(b, parity))
-        if (clock64() - t0 > budget) return false;
+        if (global_ns() - t0 > budget_ns) return false;
     return true;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -58,7 +69,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
-constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s at 2 GHz)
 
 template <int KQ, int TN, int STAGES>
 struct Tile {
@@ -77,24 +87,29 @@ struct Tile {
 // the tile's 7K/4 + 1 bulk copies in parallel.
 template <int KQ, int TN, int STAGES>
 __device__ __forceinline__ void produce(const Stencil& S, uint8_t* smem, uint64_t* full, uint64_t* empty,
-                                       int n_tiles, int* err) {
+                                       int n_tiles, int* err, const Wait W) {
     using L = Tile<KQ, TN, STAGES>;
     const unsigned lane = threadIdx.x & 31u;
     constexpr int kCopies = 7 * KQ + 1;
+    // test switch: block 0 issues nothing for its first tile (no arrival, no
+    // copies), so the consumers' bounded wait for that tile runs out
+    const bool withhold = W.withhold && blockIdx.x == 0;
     int it = 0;
     int ok = 1;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
         const int s = it % STAGES;
+        const bool skip = withhold && it == 0;
         if (lane == 0) {
-            if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, kWaitBudget)) {
+            if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, W.budget_ns)) {
                 atomicExch(err, 1);
                 ok = 0;
-            } else {
+            } else if (!skip) {
                 mbar_expect_tx(&full[s], L::kStage);
             }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
+        if (skip) continue;
         uint8_t* st = smem + s * L::kStage;
         const size_t base = (size_t)tile * TN;
         for (int c = lane; c < kCopies; c += 32) {
@@ -109,14 +124,15 @@ __device__ __forceinline__ void produce(const Stencil& S, uint8_t* smem, uint64_
         __syncwarp();
     }
     // drain: do not leave while copies may still be landing in this CTA's
-    // shared memory (bounded; the consumers normally have waited already)
+    // shared memory (bounded; the consumers normally have waited already).
+    // Every tile of the last STAGES is waited for, even after one wait ran
+    // out, so a late copy of one tile does not hide the others.
     if (lane == 0) {
         const int issued = it;
-        for (int u = (issued > STAGES ? issued - STAGES : 0); u < issued; ++u)
-            if (!mbar_wait(&full[u % STAGES], (u / STAGES) & 1, kWaitBudget)) {
-                atomicExch(err, 3);
-                break;
-            }
+        for (int u = (issued > STAGES ? issued - STAGES : 0); u < issued; ++u) {
+            if (withhold && u == 0) continue;  // nothing was issued for it
+            if (!mbar_wait(&full[u % STAGES], (u / STAGES) & 1, W.budget_ns)) atomicExch(err, 3);
+        }
     }
 }
 
@@ -136,7 +152,8 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty, int s
 template <int KQ, int TN, int STAGES, int MINB>
 __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
     bgk_step_tma(Stencil S, const float4* __restrict__ f8in, const float* __restrict__ f0in,
-                 float4* __restrict__ f8out, float* __restrict__ f0out, Collide C0, int n_tiles, int* __restrict__ err) {
+                 float4* __restrict__ f8out, float* __restrict__ f0out, Collide C0, int n_tiles, int* __restrict__ err,
+                 const Wait W) {
     using L = Tile<KQ, TN, STAGES>;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBar);
@@ -145,7 +162,7 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
     const unsigned lane = threadIdx.x & 31u;
     init_ring(full, empty, STAGES, L::kConsumers / 32);
     if (warp == L::kConsumers / 32) {
-        produce<KQ, TN, STAGES>(S, smem, full, empty, n_tiles, err);
+        produce<KQ, TN, STAGES>(S, smem, full, empty, n_tiles, err, W);
         return;
     }
     // lane = h * 8 + node-in-warp: the four lanes of a node are 8 apart, so a
@@ -156,8 +173,10 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
     int it = 0;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
         const int s = it % STAGES;
-        if (!mbar_wait(&full[s], (it / STAGES) & 1, kWaitBudget)) {
-            atomicExch(err, 2);
+        // the warp leaves together if any lane's wait ran out, so that no
+        // shuffle below waits on a lane that has left
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it / STAGES) & 1, W.budget_ns))) {
+            if (lane == 0) atomicExch(err, 2);
             return;
         }
         const uint8_t* st = smem + s * L::kStage;
@@ -291,7 +310,7 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
 template <int KQ, int TN, int STAGES, int MINB>
 __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
     tau1_step_tma(Stencil S, const float4* __restrict__ in, float4* __restrict__ out, Collide C0, int n_tiles,
-                  int* __restrict__ err) {
+                  int* __restrict__ err, const Wait W) {
     using L = Tile<KQ, TN, STAGES>;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBar);
@@ -300,7 +319,7 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
     const unsigned lane = threadIdx.x & 31u;
     init_ring(full, empty, STAGES, L::kConsumers / 32);
     if (warp == L::kConsumers / 32) {
-        produce<KQ, TN, STAGES>(S, smem, full, empty, n_tiles, err);
+        produce<KQ, TN, STAGES>(S, smem, full, empty, n_tiles, err, W);
         return;
     }
     // lane = h * 8 + node-in-warp: the four lanes of a node are 8 apart, so a
@@ -311,8 +330,10 @@ __global__ void __launch_bounds__(Tile<KQ, TN, STAGES>::kThreads, MINB)
     int it = 0;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
         const int s = it % STAGES;
-        if (!mbar_wait(&full[s], (it / STAGES) & 1, kWaitBudget)) {
-            atomicExch(err, 2);
+        // the warp leaves together if any lane's wait ran out, so that no
+        // shuffle below waits on a lane that has left
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it / STAGES) & 1, W.budget_ns))) {
+            if (lane == 0) atomicExch(err, 2);
             return;
         }
         const uint8_t* st = smem + s * L::kStage;
@@ -453,7 +474,8 @@ namespace {
 
 template <int KQ, int TN, int STAGES, int MINB>
 cudaError_t run_tma(int model, const dev::Stencil& S, const float4* a8, const float* a0, float4* b8, float* b0,
-                    const float4* ra, float4* rb, const dev::Collide& C, int* err, cudaStream_t st) {
+                    const float4* ra, float4* rb, const dev::Collide& C, int* err, const dev::Wait& W,
+                    cudaStream_t st) {
     using L = dev::Tile<KQ, TN, STAGES>;
     static_assert(L::kBytes <= 232448, "tile ring exceeds shared memory");
     const void* fn = model == 0 ? (const void*)dev::bgk_step_tma<KQ, TN, STAGES, MINB>
@@ -469,26 +491,26 @@ cudaError_t run_tma(int model, const dev::Stencil& S, const float4* a8, const fl
     const int n_tiles = (S.n + TN - 1) / TN;
     const int grid = std::max(1, std::min(n_tiles, sms * per_sm));
     if (model == 0)
-        dev::bgk_step_tma<KQ, TN, STAGES, MINB><<<grid, L::kThreads, L::kBytes, st>>>(S, a8, a0, b8, b0, C, n_tiles, err);
+        dev::bgk_step_tma<KQ, TN, STAGES, MINB><<<grid, L::kThreads, L::kBytes, st>>>(S, a8, a0, b8, b0, C, n_tiles, err, W);
     else
-        dev::tau1_step_tma<KQ, TN, STAGES, MINB><<<grid, L::kThreads, L::kBytes, st>>>(S, ra, rb, C, n_tiles, err);
+        dev::tau1_step_tma<KQ, TN, STAGES, MINB><<<grid, L::kThreads, L::kBytes, st>>>(S, ra, rb, C, n_tiles, err, W);
     return cudaGetLastError();
 }
 
 template <int KQ>
 cudaError_t run_tma_variant(int variant, int model, const dev::Stencil& S, const float4* a8, const float* a0,
                             float4* b8, float* b0, const float4* ra, float4* rb, const dev::Collide& C, int* err,
-                            cudaStream_t st) {
+                            const dev::Wait& W, cudaStream_t st) {
     // stage count from the shared-memory budget
     constexpr int kStage128 = dev::Tile<KQ, 128, 1>::kStage;
     constexpr int kStage64 = dev::Tile<KQ, 64, 1>::kStage;
     constexpr int S128 = std::min(3, 232000 / kStage128);
     constexpr int S64 = std::min(3, 232000 / kStage64);
     switch (variant) {
-        case 4: return run_tma<KQ, 128, S128, 1>(model, S, a8, a0, b8, b0, ra, rb, C, err, st);
-        case 5: return run_tma<KQ, 128, 2, 2>(model, S, a8, a0, b8, b0, ra, rb, C, err, st);
-        case 6: return run_tma<KQ, 64, S64, 2>(model, S, a8, a0, b8, b0, ra, rb, C, err, st);
-        case 7: return run_tma<KQ, 64, 2, 3>(model, S, a8, a0, b8, b0, ra, rb, C, err, st);
+        case 4: return run_tma<KQ, 128, S128, 1>(model, S, a8, a0, b8, b0, ra, rb, C, err, W, st);
+        case 5: return run_tma<KQ, 128, 2, 2>(model, S, a8, a0, b8, b0, ra, rb, C, err, W, st);
+        case 6: return run_tma<KQ, 64, S64, 2>(model, S, a8, a0, b8, b0, ra, rb, C, err, W, st);
+        case 7: return run_tma<KQ, 64, 2, 3>(model, S, a8, a0, b8, b0, ra, rb, C, err, W, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -499,13 +521,13 @@ bool tma_supported(int Kq) { return Kq == 3 || Kq == 4 || Kq == 6 || Kq == 8; }
 
 cudaError_t launch_step_tma(int variant, int model, const dev::Stencil& S, const float4* f8in, const float* f0in,
                             float4* f8out, float* f0out, const float4* rin, float4* rout, const dev::Collide& C,
-                            int* err, cudaStream_t st) {
+                            int* err, const dev::Wait& W, cudaStream_t st) {
     if (S.n == 0) return cudaSuccess;
     switch (S.Kq) {
-        case 3: return run_tma_variant<3>(variant, model, S, f8in, f0in, f8out, f0out, rin, rout, C, err, st);
-        case 4: return run_tma_variant<4>(variant, model, S, f8in, f0in, f8out, f0out, rin, rout, C, err, st);
-        case 6: return run_tma_variant<6>(variant, model, S, f8in, f0in, f8out, f0out, rin, rout, C, err, st);
-        case 8: return run_tma_variant<8>(variant, model, S, f8in, f0in, f8out, f0out, rin, rout, C, err, st);
+        case 3: return run_tma_variant<3>(variant, model, S, f8in, f0in, f8out, f0out, rin, rout, C, err, W, st);
+        case 4: return run_tma_variant<4>(variant, model, S, f8in, f0in, f8out, f0out, rin, rout, C, err, W, st);
+        case 6: return run_tma_variant<6>(variant, model, S, f8in, f0in, f8out, f0out, rin, rout, C, err, W, st);
+        case 8: return run_tma_variant<8>(variant, model, S, f8in, f0in, f8out, f0out, rin, rout, C, err, W, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -47,7 +47,29 @@ struct HostStencils {
     double bx0 = 0, by0 = 0, blx = 1, bly = 1;
     int order = 0;  // MLBM_ORDER_*
     mlbm_stencil_info info{};
+    // partitions of a node set (see PartPlan): state slots beyond the n nodes
+    // for the halo copies of other partitions' nodes, and the key that orders
+    // each node's stencil slots on the device (the unpartitioned positions, so
+    // that a partition sums its stencil in the same order; idx when empty)
+    int64_t n_halo = 0;
+    std::vector<int64_t> slot_key;  // [n][K]
 };
+
+// Partition of a node set into contiguous ranges of device positions (Hilbert
+// order): partition q owns positions [bounds[q], bounds[q + 1]); its halo is
+// every position outside the range that its nodes' stencils reference,
+// grouped by owning partition and ascending within a group.
+struct PartPlan {
+    int P = 0;
+    std::vector<int64_t> bounds;                  // [P + 1]
+    std::vector<std::vector<int64_t>> halo;       // [P][n_halo_q] positions
+    std::vector<std::vector<int64_t>> halo_off;   // [P][P + 1] start of owner o's block in halo[q]
+};
+
+mlbm_status make_part_plan(const HostStencils& H, int P, const int64_t* bounds, PartPlan& out);
+// host stencils of partition q: its owned nodes in local positions
+// 0..n_owned-1 and its halo at n_owned.., perm / inv the identity
+HostStencils slice_partition(const HostStencils& H, const PartPlan& plan, int q);
 
 }  // namespace mlbm
 

@@ -431,6 +431,44 @@ def porous(seed: int = 3, n_target: int = 1_000_000, porosity: float = 0.7, rmin
                      "mean_d": float(2 * disks[:, 2].mean()) if len(disks) else 0.0})
 
 
+def porous_batch_specs(n_samples: int = 64, first_seed: int = 1000) -> list:
+    """The batched porous configuration: sample i (seed first_seed + i) draws
+    its node count from U(50k, 400k) and its porosity from U(0.5, 0.85) with
+    its own seed; its streaming distance cycles through {1, 1/2, 1/4} and its
+    body force through {1e-6, 5e-6, 2e-5} (Darcy and inertial samples mixed).
+    tau = 1 (MLBM1) for every sample."""
+    out = []
+    for i in range(n_samples):
+        rng = np.random.default_rng(first_seed + i)
+        n = int(rng.uniform(50_000, 400_000))
+        phi = float(rng.uniform(0.5, 0.85))
+        out.append({"seed": first_seed + i, "n_target": n, "porosity": phi,
+                    "s": [1.0, 0.5, 0.25][i % 3], "g": [1e-6, 5e-6, 2e-5][i % 3]})
+    return out
+
+
+def porous_from_spec(spec: dict) -> Workload:
+    """porous() for one spec of porous_batch_specs (or any dict with seed,
+    n_target and porosity).  Porosity below ~0.55 is out of reach for
+    non-overlapping disks with a 2-spacing gap, so those samples use a gap of
+    1; the sampler keeps the porosity it reached."""
+    gap = spec.get("gap", 1.0 if spec["porosity"] < 0.6 else 2.0)
+    return porous(seed=int(spec["seed"]), n_target=int(spec["n_target"]), porosity=float(spec["porosity"]),
+                  gap=gap)
+
+
+def generate(specs: list, procs: int | None = None) -> list:
+    """porous_from_spec over many specs in a spawn-started process pool (safe
+    to use before or after CUDA is initialised in the calling process)."""
+    import multiprocessing as mp
+    import os
+    procs = procs or min(16, os.cpu_count() or 4, len(specs))
+    if procs <= 1 or len(specs) <= 1:
+        return [porous_from_spec(s) for s in specs]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(porous_from_spec, specs)
+
+
 def cylinder_array(side: float = 40.0, radius: float = 8.0, h: float = 1.0, seed: int = 0,
                    r_pd: float = 0.84, areas: str = "voronoi") -> Workload:
     """One solid disk of the given radius at the centre of a doubly periodic

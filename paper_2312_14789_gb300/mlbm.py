@@ -104,6 +104,23 @@ def lib():
                 "mlbm_batch_run_to_steady_ex": (st, [_vp, _dbl, _i64, _i64, _i64, _vp]),
                 "mlbm_batch_drag_lift": (st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
                 "mlbm_set_graphs": (st, [_vp, _i32]),
+                "mlbm_prepare_graphs": (st, [_vp]),
+                "mlbm_run_to_steady_mean": (st, [_vp, _dbl, _i64, _i64, _dbl, _i64, _vp]),
+                "mlbm_batch_run_to_steady_mean": (st, [_vp, _dbl, _i64, _i64, _vp, _i64, _vp]),
+                "mlbm_set_wait_limit": (st, [_vp, _dbl]),
+                "mlbm_partition_plan": (st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+                "mlbm_partition_nodes": (st, [_vp, _i32, _vp, _i32, _vp, _vp]),
+                "mlbm_part_init": (st, [_vp, _vp, _vp, _i32, _vp]),
+                "mlbm_part_destroy": (None, [_vp]),
+                "mlbm_part_info": (st, [_vp, _i32, _vp, _vp, _vp, _vp]),
+                "mlbm_part_set_kernel_variant": (st, [_vp, _i32]),
+                "mlbm_part_step": (st, [_vp, _i64]),
+                "mlbm_part_set_fields": (st, [_vp, _vp]),
+                "mlbm_part_get_fields": (st, [_vp, _vp]),
+                "mlbm_part_set_populations": (st, [_vp, _vp]),
+                "mlbm_part_get_populations": (st, [_vp, _vp]),
+                "mlbm_part_permeability": (st, [_vp, _vp, _vp, _vp, _vp]),
+                "mlbm_test_withhold_copy": (st, [_vp]),
                 "mlbm_reduce_scratch_doubles": (_i64, [_i64]),
                 "mlbm_reduce_fields_device": (st, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
                 "mlbm_reduce_noalloc_max_nodes": (_i64, []),
@@ -354,6 +371,28 @@ def run_to_steady(ctx: Context, tol: float, window: int, max_steps: int, raise_o
     return int(taken.value)
 
 
+def run_to_steady_mean(ctx: Context, threshold: float = 1e-2, dn: int = 20000, check: int = 1000,
+                       dt: float = 0.0, max_steps: int = 10_000_000, raise_on_max: bool = True) -> int:
+    """Steps to the paper's steady state (Sec. 3.2: relative change of the
+    mean velocity over dn steps per unit time below threshold); dt = 0: the
+    paper's units."""
+    taken = ctypes.c_int64()
+    st = lib().mlbm_run_to_steady_mean(ctx.handle, float(threshold), int(dn), int(check), float(dt), int(max_steps),
+                                       ctypes.byref(taken))
+    if st == 7 and not raise_on_max:
+        return -int(taken.value)
+    _check(st)
+    return int(taken.value)
+
+
+def set_wait_limit(ctx: Context, seconds: float):
+    _check(lib().mlbm_set_wait_limit(ctx.handle, float(seconds)))
+
+
+def test_withhold_copy(ctx: Context):
+    _check(lib().mlbm_test_withhold_copy(ctx.handle))
+
+
 def save(ctx: Context, path: str):
     _check(lib().mlbm_save(ctx.handle, path.encode()))
 
@@ -424,6 +463,17 @@ def batch_run_to_steady(ctx: Context, tol: float, window: int, max_steps: int, r
     return taken
 
 
+def batch_run_to_steady_mean(ctx: Context, threshold: float = 1e-2, dn: int = 20000, check: int = 1000, dt=None,
+                             max_steps: int = 10_000_000, raise_on_max: bool = True):
+    taken = np.empty(batch_size(ctx), np.int64)
+    d = None if dt is None else _f64(np.broadcast_to(np.asarray(dt, np.float64), (batch_size(ctx),)))
+    st = lib().mlbm_batch_run_to_steady_mean(ctx.handle, float(threshold), int(dn), int(check), _ptr(d),
+                                             int(max_steps), _ptr(taken))
+    if not (st == 7 and not raise_on_max):
+        _check(st)
+    return taken
+
+
 def batch_drag_lift(ctx: Context, ref_length, u_ref) -> dict:
     m = batch_size(ctx)
     L = _f64(np.broadcast_to(np.asarray(ref_length, np.float64), (m,)))
@@ -435,6 +485,10 @@ def batch_drag_lift(ctx: Context, ref_length, u_ref) -> dict:
 
 def set_graphs(ctx: Context, enable: bool):
     _check(lib().mlbm_set_graphs(ctx.handle, int(bool(enable))))
+
+
+def prepare_graphs(ctx: Context):
+    _check(lib().mlbm_prepare_graphs(ctx.handle))
 
 
 def reduce_scratch_doubles(n: int) -> int:
@@ -455,6 +509,86 @@ def reduce_fields_device_noalloc(rho_ptr, ux_ptr, uy_ptr, area_ptr, mask_ptr, n,
     _check(lib().mlbm_reduce_fields_device_noalloc(_vp(rho_ptr), _vp(ux_ptr), _vp(uy_ptr), _vp(area_ptr),
                                                    _vp(mask_ptr) if mask_ptr else None, int(n), _vp(out_ptr),
                                                    _vp(stream_handle) if stream_handle else None))
+
+
+# ---------------------------------------------------------- partitioned step
+def _bounds(bounds, n_parts):
+    if bounds is None:
+        return None
+    b = np.ascontiguousarray(bounds, dtype=np.int64)
+    if b.shape != (n_parts + 1,):
+        raise ValueError("bounds needs n_parts + 1 entries")
+    return b
+
+
+def partition_plan(st: Stencils, n_parts: int, bounds=None) -> dict:
+    """Host-only description of a split into n_parts position ranges."""
+    b = _bounds(bounds, n_parts)
+    out = {k: np.empty(n_parts, np.int64) for k in ("first", "n_owned", "n_halo")}
+    out["halo_from"] = np.empty((n_parts, n_parts), np.int64)
+    _check(lib().mlbm_partition_plan(st.handle, int(n_parts), _ptr(b), *[_ptr(out[k]) for k in
+                                                                        ("first", "n_owned", "n_halo", "halo_from")]))
+    return out
+
+
+def partition_nodes(st: Stencils, n_parts: int, part: int, bounds=None) -> tuple:
+    """(owned caller ids in local order, halo caller ids in slot order) of one partition."""
+    plan = partition_plan(st, n_parts, bounds)
+    owned = np.empty(int(plan["n_owned"][part]), np.int64)
+    halo = np.empty(int(plan["n_halo"][part]), np.int64)
+    _check(lib().mlbm_partition_nodes(st.handle, int(n_parts), _ptr(_bounds(bounds, n_parts)), int(part),
+                                      _ptr(owned), _ptr(halo)))
+    return owned, halo
+
+
+class Partitioned:
+    """Handle of a partitioned node set (mlbm_part_*)."""
+
+    def __init__(self, st: Stencils, params: Params, n_parts: int, bounds=None):
+        P = _Params(int(params.model), float(params.tau), float(params.tau_minus), float(params.gx), float(params.gy))
+        h = _vp()
+        b = _bounds(bounds, n_parts)
+        _check(lib().mlbm_part_init(ctypes.byref(h), st.handle, ctypes.byref(P), int(n_parts), _ptr(b)))
+        self.handle, self.n, self.n_parts, self.model, self._st = h, st.n, int(n_parts), params.model, st
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.mlbm_part_destroy(self.handle)
+            self.handle = None
+
+    def info(self, q: int) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib().mlbm_part_info(self.handle, int(q), *[ctypes.byref(x) for x in v]))
+        return dict(zip(("first", "n_owned", "n_halo", "halo_bytes_per_step"), (x.value for x in v)))
+
+    def set_kernel_variant(self, variant: int):
+        _check(lib().mlbm_part_set_kernel_variant(self.handle, int(variant)))
+
+    def step(self, n: int = 1):
+        _check(lib().mlbm_part_step(self.handle, int(n)))
+
+    def set_fields(self, ru):
+        a = _f64(ru)
+        _check(lib().mlbm_part_set_fields(self.handle, _ptr(a)))
+
+    def get_fields(self) -> np.ndarray:
+        a = np.empty((self.n, 3))
+        _check(lib().mlbm_part_get_fields(self.handle, _ptr(a)))
+        return a
+
+    def set_populations(self, f):
+        a = _f64(f)
+        _check(lib().mlbm_part_set_populations(self.handle, _ptr(a)))
+
+    def get_populations(self) -> np.ndarray:
+        a = np.empty((self.n, 9))
+        _check(lib().mlbm_part_get_populations(self.handle, _ptr(a)))
+        return a
+
+    def permeability(self) -> dict:
+        v = [ctypes.c_double() for _ in range(4)]
+        _check(lib().mlbm_part_permeability(self.handle, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("k", "u_superficial", "u_intrinsic", "tortuosity"), (x.value for x in v)))
 
 
 # ------------------------------------------------------- learned warm start

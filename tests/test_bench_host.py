@@ -1,7 +1,9 @@
-"""Host-side pieces of bench.py that need no GPU: the algorithmic byte count of
-the benchmark workload (the roofline's numerator) against the figure recorded
-in the committed ncu summary, and the rule that ties the summary's DRAM
-traffic to the step kernel source, variant and node order it was taken on."""
+"""Host-side pieces of bench.py that need no GPU: the algorithmic byte count
+(the roofline's numerator) per node kind and model, the rule that ties a
+committed ncu traffic record to the step kernel source, variant and node
+order it was taken on (and scales a smaller capture to the bench launch),
+the clock sampler's parsing, and the batched porous configuration's specs."""
+import json
 import os
 import sys
 
@@ -11,43 +13,73 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402
+from paper_2312_14789_gb300 import inputs as I  # noqa: E402
 from paper_2312_14789_gb300 import mlbm  # noqa: E402
 
 
-def _profile_fields():
-    vals = {}
-    for line in open(bench.PROFILE).read().splitlines():
-        line = line.strip()
-        if line.startswith("- ") and ":" in line:
-            k, v = line[2:].split(":", 1)
-            vals[k.strip()] = v.strip()
-    return vals
+def test_algorithmic_bytes_per_node_kind():
+    """tau = 1: 4 (3 + 3) + 24 K + 4 K + 1 = 473 B per least-squares node at
+    K = 16; BGK: 4 (9 + 9) + 24 K + 4 K + 1 = 521 B; equilibrium nodes 25 and
+    53 B; Lagrange nodes 77 and 125 B."""
+    info = {"n_wls": 10, "n_lagrange": 3, "n_eq": 2}
+    assert bench.algorithmic_bytes(info, 16, "tau1") == 10 * 473 + 3 * 77 + 2 * 25
+    assert bench.algorithmic_bytes(info, 16, "bgk") == 10 * 521 + 3 * 125 + 2 * 53
+    assert bench.algorithmic_bytes(info, 12, "bgk") == 10 * 409 + 3 * 125 + 2 * 53
+    w = I.porous(seed=5, n_target=3000, porosity=0.7)
+    st = mlbm.build_stencils_for(w, K=16, s=1.0, bb_mode=mlbm.BB_INTERPOLATED)
+    i = mlbm.stencils_info(st)
+    assert i["n_wls"] + i["n_lagrange"] + i["n_eq"] == w.n
+    assert bench.algorithmic_bytes(i, 16, "tau1") == i["n_wls"] * 473 + i["n_lagrange"] * 77
 
 
-def test_algorithmic_bytes_of_the_bench_workload_match_the_profile():
-    """Per node kind: 4 (9 + 9) + 24 K + 4 K + 1 bytes for a least-squares node,
-    16 + 36 + 1 for an equilibrium node; the six runs of the sweep."""
-    w = bench.make_workload()
-    st_by_s = {s: mlbm.build_stencils_for(w, K=16, s=s, bb_mode=mlbm.BB_SIMPLE)
-               for s in sorted({s for _, s in bench.CASES})}
-    infos = [mlbm.stencils_info(st_by_s[s]) for _, s in bench.CASES]
-    total = sum(bench.algorithmic_bytes(i, 16) for i in infos)
-    n_wls = sum(i["n_wls"] for i in infos)
-    n_eq = sum(i["n_eq"] for i in infos)
-    assert sum(i["n_lagrange"] for i in infos) == 0
-    assert total == n_wls * 521 + n_eq * 53
-    assert total == int(_profile_fields()["algorithmic_bytes_per_launch"])
+def test_traffic_record_applies_only_to_its_kernel_and_scales(tmp_path, monkeypatch):
+    rec = {"kernel_source_hash": bench.kernel_source_hash(), "kernel_variant": 26, "node_order": "hilbert",
+           "dram_bytes_per_launch": 1.0e9, "node_updates_per_launch": 2_000_000}
+    p = tmp_path / "t.json"
+    p.write_text(json.dumps(rec))
+    monkeypatch.setitem(bench.TRAFFIC, "porous_batch", str(p))
+    assert bench.measured_traffic("porous_batch", 26, 0) == 1.0e9
+    assert bench.measured_traffic("porous_batch", 26, 0, node_updates=6_000_000) == pytest.approx(3.0e9)
+    assert bench.measured_traffic("porous_batch", 25, 0) is None
+    assert bench.measured_traffic("porous_batch", 26, 1) is None
+    rec["kernel_source_hash"] = "0" * 16
+    p.write_text(json.dumps(rec))
+    assert bench.measured_traffic("porous_batch", 26, 0) is None
+    monkeypatch.setitem(bench.TRAFFIC, "porous_batch", str(tmp_path / "missing.json"))
+    assert bench.measured_traffic("porous_batch", 26, 0) is None
 
 
-def test_profile_traffic_applies_only_to_its_kernel_source_variant_and_order():
-    f = _profile_fields()
-    variant = int(f["kernel_variant"])
-    order = bench.ORDER_NAMES.index(f["node_order"])
-    if f["kernel_source_hash"] != bench.kernel_source_hash():
-        pytest.skip("the step kernel source changed since the summary was taken")
-    t = bench.measured_traffic(variant, order)
-    assert t == float(f["dram_bytes_per_launch"])
-    # within a few percent of the algorithmic bytes: nothing re-read
-    assert 0.99 <= t / int(f["algorithmic_bytes_per_launch"]) <= 1.02
-    assert bench.measured_traffic(variant + 1, order) is None
-    assert bench.measured_traffic(variant, (order + 1) % len(bench.ORDER_NAMES)) is None
+def test_committed_traffic_records_are_consistent():
+    """Each committed record names its capture and lies within a few percent
+    of the algorithmic bytes of the launch it was taken on."""
+    for path in bench.TRAFFIC.values():
+        if not os.path.exists(path):
+            continue
+        rec = json.load(open(path))
+        for k in ("kernel_source_hash", "kernel_variant", "node_order", "dram_bytes_per_launch",
+                  "algorithmic_bytes_per_launch", "command"):
+            assert k in rec, (path, k)
+        assert 0.95 <= rec["dram_bytes_per_launch"] / rec["algorithmic_bytes_per_launch"] <= 1.10
+
+
+def test_clock_parsing():
+    out = "\n".join([
+        "2070, 2070, 300.1, 0, Not Active, Not Active, Not Active, Not Active",
+        "1965, 2070, 1200.5, 100, Not Active, Not Active, Not Active, Active",
+        "1980, 2070, 1210.5, 99, Not Active, Not Active, Not Active, Active",
+        "2010, 2070, 1100.0, 97, Not Active, Not Active, Not Active, Not Active",
+    ])
+    c = bench.Clocks.parse(out)
+    assert c["sm_mhz"] == 1980 and c["sm_max_mhz"] == 2070
+    assert c["reasons"] == ["sw_power_cap"] and c["samples"] == 4 and c["samples_under_load"] == 3
+
+
+def test_porous_batch_specs():
+    a = I.porous_batch_specs(64)
+    assert len(a) == 64 and a[0]["seed"] == 1000 and a[-1]["seed"] == 1063
+    assert all(50_000 <= s["n_target"] < 400_000 and 0.5 <= s["porosity"] < 0.85 for s in a)
+    assert [s["s"] for s in a[:4]] == [1.0, 0.5, 0.25, 1.0]
+    assert [s["g"] for s in a[:3]] == [1e-6, 5e-6, 2e-5]
+    # seeds decide the samples: a later rank's set continues the sequence
+    b = I.porous_batch_specs(4, first_seed=1002)
+    assert b[0]["n_target"] == a[2]["n_target"] and b[0]["porosity"] == a[2]["porosity"]

@@ -3,8 +3,15 @@
 Forward and gradients: the oracle runs with the kernels' BF16 rounding points
 (features, weights, hidden activations, output and hidden errors rounded to
 BF16, everything else exact), so the only difference left is FP32
-accumulation order and the rare BF16 rounding flip it causes; the bound is a
-relative L2 error of 1e-3 per output / per parameter tensor.
+accumulation order and the rare BF16 rounding flip it causes.  Element by
+element, per output column and per parameter tensor:
+  * every element within 5e-3 of the column's / tensor's largest magnitude
+    (one BF16 flip of a hidden value moves an output by about 2^-8 times one
+    weight times that value, a few 1e-4 of the scale, while a wrong row, a
+    transposed weight block or a dropped term moves elements by O(scale));
+  * at least 99.5% of the elements within 1e-4 of that scale plus 1e-3 of
+    their own magnitude (the FP32 accumulation order alone);
+and the relative L2 error of each column / tensor at most 1e-3.
 """
 import numpy as np
 import pytest
@@ -26,6 +33,19 @@ def M():
 
 def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, float) - np.asarray(b, float)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _assert_elementwise(a, b, what):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    assert a.shape == b.shape, what
+    scale = float(np.max(np.abs(b))) if b.size else 0.0
+    d = np.abs(a - b)
+    worst = int(np.argmax(d)) if d.size else 0
+    assert np.all(d <= 5e-3 * scale), (what, worst, float(d.flat[worst]), scale)
+    tight = d <= 1e-4 * scale + 1e-3 * np.abs(b)
+    assert tight.mean() >= 0.995, (what, float(tight.mean()))
+    assert _rel(a, b) <= 1e-3, (what, _rel(a, b))
 
 
 def _params(seed, bias_scale=0.1, n_out=2):
@@ -60,7 +80,8 @@ def test_forward_matches_oracle(M, n, n_out):
     torch.cuda.synchronize()
     Y = Yd.cpu().numpy()
     Yo, _ = OM.forward(p64, X.astype(np.float32).astype(np.float64), bf16_round=True)
-    assert _rel(Y, Yo) <= 1e-3
+    for j in range(n_out):
+        _assert_elementwise(Y[:, j], Yo[:, j], f"output column {j}")
 
 
 def test_forward_empty(M):
@@ -85,7 +106,7 @@ def test_gradients_match_oracle(M, n, n_out):
     l_or = OM.loss(p64, X.astype(np.float64), T.astype(np.float64), bf16_round=True)
     assert abs(loss - l_or) <= 1e-3 * l_or
     for k, (a, b) in enumerate(zip(g_gpu, g_or)):
-        assert _rel(a, b) <= 1e-3, (k, _rel(a, b))
+        _assert_elementwise(a, b, f"parameter tensor {k}")
 
 
 def test_gradients_reproducible(M):
