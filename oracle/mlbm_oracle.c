@@ -538,7 +538,10 @@ void oracle_mlbm_step(int64_t n, const double* f_in, int64_t nt, const int64_t* 
                       const double* eq_val, double tau_p, double tau_m, double gx, double gy,
                       double* f_out) {
     (void)n;
-#pragma omp parallel for schedule(static)
+    /* small node sets run on one thread: the fork and join of a parallel
+       region would cost more than the step (every node is independent, so
+       the result does not depend on the thread count) */
+#pragma omp parallel for schedule(static) if (nt >= 16384)
     for (int64_t t = 0; t < nt; ++t) {
         int64_t i = targets ? targets[t] : t;
         double f[9];
@@ -571,7 +574,7 @@ void oracle_mlbm1_step(int64_t n, const double* ru_in, int64_t nt, const int64_t
                        const int64_t* idx, const double* W, const int* src, const uint8_t* node_class,
                        const double* eq_val, double gx, double gy, double* ru_out) {
     (void)n;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (nt >= 16384)
     for (int64_t t = 0; t < nt; ++t) {
         int64_t i = targets ? targets[t] : t;
         if (node_class[i] == 2) {
