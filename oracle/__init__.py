@@ -79,6 +79,9 @@ def lib():
                                           vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.oracle_rbf_weights.restype = i32
             L.oracle_rbf_weights.argtypes = [vp, i32, dbl, dbl, vp]
+            L.oracle_rbf_lagrangian.restype = None
+            L.oracle_rbf_lagrangian.argtypes = [i64, vp, vp, i64, vp, i32, i32, dbl, i32, i32, vp, vp, vp, vp, i32,
+                                                vp, i32, vp, vp, vp]
             L.oracle_mlbm_step.restype = None
             L.oracle_mlbm_step.argtypes = [i64, vp, i64, vp, i32, vp, vp, vp, vp, vp, dbl, dbl, dbl, dbl, vp]
             L.oracle_mlbm1_step.restype = None
@@ -231,7 +234,11 @@ class Operator:
     workload, either for all nodes or for a subset `targets`."""
 
     def __init__(self, w, K, s, sigma_factor=0.7071067811865476, bb_mode=1, use_lagrange=True,
-                 lag_tol=1e-9, targets=None, interp="wls"):
+                 lag_tol=1e-9, targets=None, interp="wls", n_l=25, k_max=None):
+        """interp: "wls" (least squares over the node's K-stencil), "rbf"
+        (RBF-FD over the node's K-stencil) or "rbf_points" (RBF-FD with the
+        n_l nearest nodes of every departure point, Sec. 2.2; the stencil
+        becomes the union of those, k_max slots)."""
         self.w = w
         self.K, self.s, self.bb_mode = int(K), float(s), int(bb_mode)
         self.sigma_factor = float(sigma_factor)
@@ -257,7 +264,7 @@ class Operator:
         xy = _c(w.xy, np.float64)
         lib().oracle_assemble(nt, _p(self.targets), K, _p(self.idx), _p(self.off), _p(xy), _p(cls),
                               self.s, self.sigma_factor, self.bb_mode, int(bool(use_lagrange)),
-                              {"wls": 0, "rbf": 1}[interp],
+                              {"wls": 0, "rbf": 1, "rbf_points": 0}[interp],
                               float(lag_tol), _p(box), _p(side), _p(disks) if len(disks) else None,
                               len(disks), _p(self.kind), _p(self.M), _p(self.lag_slot), _p(self.lag_h),
                               _p(self.lag_center), _p(self.link), _p(self.q), _p(self.W), _p(self.src),
@@ -265,6 +272,16 @@ class Operator:
         self.eq_val = _c(w.eq_values, np.float64)
         self.node_class = cls
         self.area = _c(w.area, np.float64)
+        self.idx_own = self.idx
+        if interp == "rbf_points":
+            kmax = int(k_max or 4 * K)
+            idx2 = np.empty((nt, kmax), np.int64)
+            W2 = np.empty((nt, 9, kmax))
+            lib().oracle_rbf_lagrangian(nt, _p(self.targets), _p(xy), w.n, _p(box), int(periodic[0]),
+                                        int(periodic[1]), self.s, int(n_l), K, _p(self.idx),
+                                        _p(_c(self.kind, np.int32)), _p(_c(self.link, np.int32)), _p(self.q),
+                                        self.bb_mode, _p(self.W), kmax, _p(idx2), _p(W2), _p(self.status))
+            self.idx, self.W, self.K = idx2, W2, kmax
 
     @property
     def target_ids(self):
@@ -351,7 +368,7 @@ def wall_stress_force(op: Operator, ru, tau, nodes, normals, ds):
     for i, n, l in zip(np.asarray(nodes, np.int64), np.asarray(normals, np.float64), np.asarray(ds, np.float64)):
         if op.kind[i] != 0:
             raise ValueError(f"node {i} is not a least-squares node")
-        j = op.idx[i]
+        j = op.idx_own[i]
         du = ru[j, 1] - ru[i, 1]
         dv = ru[j, 2] - ru[i, 2]
         ux_x, ux_y = op.M[i, 1] @ du, op.M[i, 2] @ du

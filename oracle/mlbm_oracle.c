@@ -725,3 +725,118 @@ void oracle_assemble(int64_t nt, const int64_t* targets, int K, const int64_t* i
         }
     }
 }
+
+/* ----------------------------------- RBF-FD per Lagrangian point --- */
+/*
+ * The paper's RBF-FD stencils (Sec. 2.2): every Lagrangian (departure) point
+ * is interpolated from its own N_L nearest nodes (the paper uses N_L = 25).
+ * This rewrites the rows that oracle_assemble gave the least-squares-class
+ * nodes (kind 0): for every direction k = 1..8 that interpolates (all but
+ * simple bounce-back links; the departure rule of oracle_assemble, so an
+ * interpolated link uses its reflected point), the n_l nearest nodes of the
+ * departure point x_i + d_k -- squared distance from that point, offsets by
+ * the periodic minimum image from x_i, ties to the lower node id, brute
+ * force -- carry the cubic-PHS + quadratic weights of oracle_rbf_weights
+ * there.  The node's stencil becomes the union of the node itself and its
+ * directions' stencils in increasing node id, padded to kmax slots with the
+ * node itself at zero weight; every other node keeps its own K-node stencil
+ * in the first K slots, padded the same way, with its rows copied.
+ * idx_out [nt][kmax], w_out [nt][9][kmax] (row 0 zero).  status[t]: 3 when
+ * the union has more than kmax members, 2 on a singular system.
+ */
+void oracle_rbf_lagrangian(int64_t nt, const int64_t* targets, const double* xy, int64_t n, const double* box,
+                           int periodic_x, int periodic_y, double s, int n_l, int K, const int64_t* idx,
+                           const int* kind, const int* link, const double* q, int bb_mode, const double* w_in,
+                           int kmax, int64_t* idx_out, double* w_out, int* status) {
+    const double Lx = box[2] - box[0], Ly = box[3] - box[1];
+#pragma omp parallel
+    {
+    double* bd = (double*)malloc(sizeof(double) * n_l);
+    int64_t* bi = (int64_t*)malloc(sizeof(int64_t) * n_l);
+    double* bo = (double*)malloc(sizeof(double) * 2 * n_l);
+    int64_t* uni = (int64_t*)malloc(sizeof(int64_t) * (8 * n_l + 1));
+    int64_t* memb = (int64_t*)malloc(sizeof(int64_t) * 8 * n_l);
+    double* wk = (double*)malloc(sizeof(double) * 8 * n_l);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        const int64_t i = targets ? targets[t] : t;
+        for (int j = 0; j < kmax; ++j) idx_out[t * kmax + j] = i;
+        for (int j = 0; j < 9 * kmax; ++j) w_out[t * 9 * kmax + j] = 0.0;
+        if (kind[t] != 0) {
+            if (K > kmax) { status[t] = 3; continue; }
+            for (int j = 0; j < K; ++j) idx_out[t * kmax + j] = idx[t * K + j];
+            for (int k = 0; k < 9; ++k)
+                for (int j = 0; j < K; ++j) w_out[(t * 9 + k) * kmax + j] = w_in[(t * 9 + k) * K + j];
+            continue;
+        }
+        double dx[9], dy[9];
+        int use[9];
+        odepartures(s, link + 9 * t, q + 9 * t, bb_mode, dx, dy, use);
+        const double xi = xy[2 * i], yi = xy[2 * i + 1];
+        int nu = 0;
+        uni[nu++] = i;
+        for (int k = 1; k < 9; ++k) {
+            if (!use[k]) continue;
+            int cnt = 0;
+            for (int64_t j = 0; j < n; ++j) {
+                const double ox = omin_image(xy[2 * j] - xi, Lx, periodic_x);
+                const double oy = omin_image(xy[2 * j + 1] - yi, Ly, periodic_y);
+                const double ex = ox - dx[k], ey = oy - dy[k];
+                const double d2 = ex * ex + ey * ey;
+                if (cnt == n_l) {
+                    if (d2 > bd[n_l - 1] || (d2 == bd[n_l - 1] && j > bi[n_l - 1])) continue;
+                    cnt--;
+                }
+                int pos = cnt;
+                while (pos > 0 && (bd[pos - 1] > d2 || (bd[pos - 1] == d2 && bi[pos - 1] > j))) {
+                    bd[pos] = bd[pos - 1];
+                    bi[pos] = bi[pos - 1];
+                    bo[2 * pos] = bo[2 * pos - 2];
+                    bo[2 * pos + 1] = bo[2 * pos - 1];
+                    pos--;
+                }
+                bd[pos] = d2;
+                bi[pos] = j;
+                bo[2 * pos] = ox;
+                bo[2 * pos + 1] = oy;
+                cnt++;
+            }
+            const int st = oracle_rbf_weights(bo, n_l, dx[k], dy[k], wk + (k - 1) * n_l);
+            if (st) { status[t] = st; break; }
+            for (int m = 0; m < n_l; ++m) {
+                memb[(k - 1) * n_l + m] = bi[m];
+                int seen = 0;
+                for (int u = 0; u < nu; ++u) if (uni[u] == bi[m]) { seen = 1; break; }
+                if (!seen) uni[nu++] = bi[m];
+            }
+        }
+        if (status[t]) continue;
+        if (nu > kmax) { status[t] = 3; continue; }
+        /* union in increasing node id */
+        for (int a = 1; a < nu; ++a) {
+            const int64_t v = uni[a];
+            int b = a;
+            while (b > 0 && uni[b - 1] > v) { uni[b] = uni[b - 1]; b--; }
+            uni[b] = v;
+        }
+        for (int u = 0; u < nu; ++u) idx_out[t * kmax + u] = uni[u];
+        for (int k = 0; k < 9; ++k) {
+            if (k == 0 || !use[k]) {
+                /* the rest population and simple bounce-back: the rows of
+                   oracle_assemble (one-hot on the node), moved to its slot */
+                for (int j = 0; j < K; ++j) {
+                    const double wv = w_in[(t * 9 + k) * K + j];
+                    if (wv == 0.0) continue;
+                    for (int u = 0; u < nu; ++u)
+                        if (uni[u] == idx[t * K + j]) { w_out[(t * 9 + k) * kmax + u] += wv; break; }
+                }
+                continue;
+            }
+            for (int m = 0; m < n_l; ++m)
+                for (int u = 0; u < nu; ++u)
+                    if (uni[u] == memb[(k - 1) * n_l + m]) { w_out[(t * 9 + k) * kmax + u] = wk[(k - 1) * n_l + m]; break; }
+        }
+    }
+    free(bd); free(bi); free(bo); free(uni); free(memb); free(wk);
+    }
+}
