@@ -61,7 +61,7 @@ enum { MLBM_BB_SIMPLE = 0, MLBM_BB_INTERPOLATED = 1 };
 enum { MLBM_MODEL_BGK = 0, MLBM_MODEL_TAU1 = 1 };
 /* interpolant of the scattered (non-Lagrange) nodes: quadratic weighted least
    squares, or RBF-FD (cubic polyharmonic spline with quadratic terms, Sec. 2.2) */
-enum { MLBM_INTERP_WLS = 0, MLBM_INTERP_RBF = 1 };
+enum { MLBM_INTERP_WLS = 0, MLBM_INTERP_RBF = 1, MLBM_INTERP_RBF_POINTS = 2 };
 /* device node order: Hilbert curve (default), Morton (Z) curve, strips of
    about 8 node spacings left to right, or the caller's order */
 enum { MLBM_ORDER_HILBERT = 0, MLBM_ORDER_MORTON = 1, MLBM_ORDER_ROWS = 2, MLBM_ORDER_INPUT = 3 };
@@ -137,6 +137,26 @@ mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_geometry* ge
 mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
                                    double sigma_factor, int bb_mode, int use_lagrange, int interp,
                                    mlbm_stencils** out);
+
+/*
+ * The paper's RBF-FD with a stencil per Lagrangian point (Sec. 2.2: each
+ * departure point is interpolated from its own N_L nearest nodes; the paper
+ * uses N_L = 25).  For every interpolating direction of a scattered node,
+ * the n_l nearest nodes of its departure point x - s e_k (of the reflected
+ * point x + (1 - 2q) s e_k for an interpolated bounce-back link) -- squared
+ * distance from that point, periodic minimum images, ties to the lower
+ * node id -- carry the cubic-PHS + quadratic weights there (FP64 LU).  The
+ * node's device stencil is the union of the node and its directions'
+ * stencils, k_max slots wide (unused slots hold the node at zero weight),
+ * with 8 rows of k_max FP32 weights.  Lagrange detection, links and the
+ * node's own fit use its 16 nearest nodes, as mlbm_build_stencils with
+ * K = 16.  n_l in [7, 32] (<= n), k_max a multiple of 4 in [16, 64].
+ * Errors: as mlbm_build_stencils; MLBM_E_INVALID (naming the node) when a
+ * union holds more than k_max nodes.  The scattered nodes of such stencils
+ * run the RBF-FD step kernels (K = k_max); K > 32 runs variants 0-3 only.
+ */
+mlbm_status mlbm_build_stencils_points(const mlbm_nodes* nodes, const mlbm_geometry* geo, int n_l, int k_max,
+                                       double s, int bb_mode, int use_lagrange, mlbm_stencils** out);
 
 void mlbm_stencils_free(mlbm_stencils* st);
 
@@ -237,6 +257,9 @@ int64_t mlbm_step_count(const mlbm_ctx* ctx);
  * least-squares contexts only (else MLBM_E_INVALID); a listed node that is not
  * a least-squares node, or an id out of range, gives MLBM_E_INVALID.  Arrays
  * are caller-owned host memory, read during the call; m = 0 gives F = 0.
+ * The context keeps a device buffer for 48 bytes per wall node, allocated on
+ * the first call and grown only when a call lists more nodes than any before
+ * (then MLBM_E_OOM if it cannot), so repeated calls allocate nothing.
  */
 mlbm_status mlbm_wall_stress_force(mlbm_ctx* ctx, const int64_t* nodes, const double* normals, const double* ds,
                                    int64_t m, double* fx, double* fy);
@@ -396,6 +419,12 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  *        on the SM slots it frees, and the next grid prefetches its first
  *        stencil rows into L2 before it waits for the previous grid's writes
  *        (BGK and tau = 1; RBF-FD stencils run the plain capped kernel)
+ *   27-29 persistent CTAs of one lane per node (the node code of 11) whose
+ *        matrix, index and meta rows come from a shared-memory ring that a
+ *        producer warp fills with bulk async copies, as 4-7: 27 = 128-node
+ *        tiles, 2 stages, 2 CTAs/SM; 28 = 64-node tiles, 2 stages, 3 CTAs/SM;
+ *        29 = 64-node tiles, 3 stages, 2 CTAs/SM (BGK and tau = 1; RBF-FD
+ *        stencils run the plain capped kernel)
  * Variants 4 and up are available for K = 12, 16, 24 and 32.
  * The default is 25 when available, else 1.  mlbm_autotune times every
  * available variant for steps_per_variant steps on the context's stream
@@ -404,6 +433,10 @@ double mlbm_last_step_ms(const mlbm_ctx* ctx);
  */
 mlbm_status mlbm_set_kernel_variant(mlbm_ctx* ctx, int variant);
 int mlbm_kernel_variant(const mlbm_ctx* ctx);
+/* Per-step times (ms) of the last mlbm_autotune(_ex) on this context:
+   ms[v] for variants v = 0 .. n-1 (-1: not timed there, or no autotune yet).
+   Returns the number of variants, or -1 for a NULL context. */
+int mlbm_autotune_times(const mlbm_ctx* ctx, double* ms, int n);
 mlbm_status mlbm_autotune(mlbm_ctx* ctx, int steps_per_variant, double* best_ms);
 /* As mlbm_autotune; with flush_l2 != 0 every timed step is preceded by a
    read of a zeroed 512 MiB temporary device buffer, so that steps are timed

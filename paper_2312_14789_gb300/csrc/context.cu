@@ -83,11 +83,17 @@ struct mlbm_ctx {
     // and the test switch that makes the next launch withhold one tile
     unsigned long long wait_ns = 2000000000ULL;
     int withhold_next = 0;
+    // device buffer of mlbm_wall_stress_force, grown on demand and kept:
+    // positions, normals, lengths and tractions of up to wall_cap wall nodes
+    uint8_t* wall_buf = nullptr;
+    int64_t wall_cap = 0;
+    // per-step time of every variant in the last autotune (-1: not timed)
+    std::vector<double> tune_ms;
 };
 
 namespace {
 constexpr int kGraphSteps = 16;
-constexpr int kMaxVariant = 26;  // step kernel variants 0..26 (see mlbm_set_kernel_variant)
+constexpr int kMaxVariant = 29;  // step kernel variants 0..29 (see mlbm_set_kernel_variant)
 }
 
 // Cold-cache start for timed steps: reading a zeroed buffer several times the
@@ -190,11 +196,15 @@ mlbm_status sync(mlbm_ctx* c) {
 mlbm_status launch_one_step(mlbm_ctx* c, int variant) {
     const int a = c->cur, b = c->cur ^ 1;
     const int model = c->params.model == MLBM_MODEL_BGK ? 0 : 1;
-    if (variant >= 4 && variant <= 7 && !c->S.Wr) {
+    if (((variant >= 4 && variant <= 7) || (variant >= 27 && variant <= 29)) && !c->S.Wr) {
         const dev::Wait W{c->wait_ns, c->withhold_next};
         c->withhold_next = 0;
-        MLBM_CUDA(launch_step_tma(variant, model, c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->ruv[a], c->ruv[b],
-                                  c->C, c->err, W, c->stream));
+        if (variant <= 7)
+            MLBM_CUDA(launch_step_tma(variant, model, c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->ruv[a],
+                                      c->ruv[b], c->C, c->err, W, c->stream));
+        else
+            MLBM_CUDA(launch_step_ring1(variant, model, c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->ruv[a],
+                                        c->ruv[b], c->C, c->err, W, c->stream));
     }
     else if (model == 0)
         MLBM_CUDA(launch_bgk_step(c->S, c->f8[a], c->f0[a], c->f8[b], c->f0[b], c->C, variant, c->stream));
@@ -221,7 +231,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     const int64_t nps = (H.n + H.n_halo + 127) / 128 * 128;
     const int K = H.K, Kq = K / 4;
     // ---- host-side device layout
-    const bool rbf = H.interp == MLBM_INTERP_RBF;
+    const bool rbf = H.interp != MLBM_INTERP_WLS;  // per-direction RBF-FD weights
     std::vector<int32_t> hidx((size_t)Kq * np * 4, 0);
     std::vector<float> hM((size_t)6 * Kq * np * 4, 0.f);
     std::vector<float> hW(rbf ? (size_t)8 * Kq * np * 4 : 0, 0.f);
@@ -505,6 +515,7 @@ void free_ctx(mlbm_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     for (void* p : c->allocations) cudaFree(p);
+    if (c->wall_buf) cudaFree(c->wall_buf);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -769,7 +780,7 @@ mlbm_status mlbm_set_wait_limit(mlbm_ctx* c, double seconds) {
 
 mlbm_status mlbm_test_withhold_copy(mlbm_ctx* c) {
     if (!c) return set_error(MLBM_E_INVALID, "test_withhold_copy: NULL context");
-    if (c->variant < 4 || c->variant > 7 || c->S.Wr)
+    if (!((c->variant >= 4 && c->variant <= 7) || (c->variant >= 27 && c->variant <= 29)) || c->S.Wr)
         return set_error(MLBM_E_INVALID, "test_withhold_copy: the context's kernel variant has no bulk-copy ring");
     c->withhold_next = 1;
     return MLBM_OK;
@@ -817,15 +828,31 @@ mlbm_status mlbm_wall_stress_force(mlbm_ctx* c, const int64_t* nodes, const doub
     }
     double sx = 0.0, sy = 0.0;
     if (m > 0) {
-        int* dpos = nullptr;
-        double *dn = nullptr, *dds = nullptr, *dout = nullptr;
         const size_t mm = (size_t)m;
-        cudaError_t e = cudaMalloc(&dpos, mm * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&dn, mm * 16);
-        if (e == cudaSuccess) e = cudaMalloc(&dds, mm * 8);
-        if (e == cudaSuccess) e = cudaMalloc(&dout, mm * 16);
+        if (m > c->wall_cap) {  // grow (rare: the wall node list is usually fixed)
+            if (c->wall_buf) {
+                MLBM_CUDA(cudaStreamSynchronize(c->stream));
+                cudaFree(c->wall_buf);
+                c->wall_buf = nullptr;
+                c->wall_cap = 0;
+            }
+            void* q = nullptr;
+            cudaError_t e = cudaMalloc(&q, mm * 48);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                return set_error(MLBM_E_OOM, std::string("wall_stress_force: cudaMalloc: ") + cudaGetErrorString(e));
+            }
+            c->wall_buf = static_cast<uint8_t*>(q);
+            c->wall_cap = m;
+        }
+        // normals | tractions | lengths | positions (16-, 16-, 8-, 4-byte items)
+        const size_t cap = (size_t)c->wall_cap;
+        double* dn = reinterpret_cast<double*>(c->wall_buf);
+        double* dout = reinterpret_cast<double*>(c->wall_buf + cap * 16);
+        double* dds = reinterpret_cast<double*>(c->wall_buf + cap * 32);
+        int* dpos = reinterpret_cast<int*>(c->wall_buf + cap * 40);
         std::vector<double> out(2 * mm, 0.0);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dpos, pos.data(), mm * 4, cudaMemcpyHostToDevice, c->stream);
+        cudaError_t e = cudaMemcpyAsync(dpos, pos.data(), mm * 4, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dn, normals, mm * 16, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dds, ds, mm * 8, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) {
@@ -836,10 +863,6 @@ mlbm_status mlbm_wall_stress_force(mlbm_ctx* c, const int64_t* nodes, const doub
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), dout, mm * 16, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        cudaFree(dpos);
-        cudaFree(dn);
-        cudaFree(dds);
-        cudaFree(dout);
         if (e != cudaSuccess) return set_error(MLBM_E_CUDA, std::string("wall_stress_force: ") + cudaGetErrorString(e));
         for (size_t i = 0; i < mm; ++i) {  // fixed order: reproducible
             if (std::isnan(out[2 * i])) return set_error(MLBM_E_INVALID, "wall_stress_force: node " +
@@ -977,6 +1000,13 @@ mlbm_status mlbm_set_kernel_variant(mlbm_ctx* c, int variant) {
 
 int mlbm_kernel_variant(const mlbm_ctx* c) { return c ? c->variant : -1; }
 
+int mlbm_autotune_times(const mlbm_ctx* c, double* ms, int n) {
+    if (!c) return -1;
+    for (int v = 0; v < n && v <= kMaxVariant; ++v)
+        ms[v] = v < (int)c->tune_ms.size() ? c->tune_ms[v] : -1.0;
+    return kMaxVariant + 1;
+}
+
 mlbm_status mlbm_autotune(mlbm_ctx* c, int steps_per_variant, double* best_ms) {
     return mlbm_autotune_ex(c, steps_per_variant, 0, best_ms);
 }
@@ -1025,6 +1055,7 @@ mlbm_status mlbm_autotune_ex(mlbm_ctx* c, int steps_per_variant, int flush_l2, d
     }
     int best = c->variant;
     double best_t = 1e30;
+    c->tune_ms.assign(kMaxVariant + 1, -1.0);
     for (int v = 0; v <= kMaxVariant && st == MLBM_OK; ++v) {
         if (v >= 14 && v <= 24 && c->params.model != MLBM_MODEL_BGK) continue;
         if (v >= 4 && !tma_supported(c->K / 4)) continue;
@@ -1068,6 +1099,7 @@ mlbm_status mlbm_autotune_ex(mlbm_ctx* c, int steps_per_variant, int flush_l2, d
             cudaEventElapsedTime(&ms, c->ev0, c->ev1);
             per = ms / steps_per_variant;
         }
+        c->tune_ms[v] = per;
         if (per < best_t) {
             best_t = per;
             best = v;
@@ -1144,7 +1176,7 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
             node_sample[o + p] = (uint16_t)i;
         }
         std::copy(H.M.begin(), H.M.end(), C.M.begin() + (size_t)o * 6 * K);
-        if (C.interp == MLBM_INTERP_RBF) {
+        if (C.interp != MLBM_INTERP_WLS) {
             if (C.Wr.empty()) C.Wr.assign((size_t)n * 8 * K, 0.0);
             std::copy(H.Wr.begin(), H.Wr.end(), C.Wr.begin() + (size_t)o * 8 * K);
         }

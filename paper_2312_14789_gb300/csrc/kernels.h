@@ -18,6 +18,12 @@ cudaError_t launch_wall_traction(const dev::Stencil& S, int model, const float4*
                                  const double* nrm, const double* ds, int m, double* out, cudaStream_t st);
 // raises the dynamic shared-memory limit of the staged step kernel (variant 22)
 cudaError_t prepare_staged_step(int Kq, int stage_max);
+// RBF-FD stencils (kernels_rbf.cu); launch_bgk_step / launch_tau1_step hand
+// contexts with per-direction weights to these
+cudaError_t launch_bgk_step_rbf(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,
+                                float* f0out, const dev::Collide& C, int variant, cudaStream_t st);
+cudaError_t launch_tau1_step_rbf(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C,
+                                 int variant, cudaStream_t st);
 cudaError_t launch_tau1_step(const dev::Stencil& S, const float4* in, float4* out, const dev::Collide& C, int variant,
                              cudaStream_t st);
 cudaError_t launch_set_bgk(int n, const int* perm, const double* f, float4* f8, float* f0, cudaStream_t st);
@@ -35,6 +41,11 @@ bool tma_supported(int Kq);
 cudaError_t launch_step_tma(int variant, int model, const dev::Stencil& S, const float4* f8in, const float* f0in,
                             float4* f8out, float* f0out, const float4* rin, float4* rout, const dev::Collide& C,
                             int* err, const dev::Wait& W, cudaStream_t st);
+// persistent one-lane-per-node step with a bulk-copy ring of stencil rows
+// (kernels.cu), variants 27..29
+cudaError_t launch_step_ring1(int variant, int model, const dev::Stencil& S, const float4* f8in, const float* f0in,
+                              float4* f8out, float* f0out, const float4* rin, float4* rout, const dev::Collide& C,
+                              int* err, const dev::Wait& W, cudaStream_t st);
 int force_blocks(int n_link_nodes);
 cudaError_t launch_force(const dev::Stencil& S, int model, int n_link_nodes, const int* link_nodes,
                          const float* area_over_s2, const float4* f8, const float4* ruv, const dev::Collide& C,

@@ -140,6 +140,74 @@ void knn_one(const CellGrid& g, const double* xy, const Box& b, int64_t i, int K
     }
 }
 
+// The n_l nearest nodes of the point x_i + (dx, dy), ordered by (d2, id):
+// offsets by the periodic minimum image from node i, the squared distance
+// measured from the point (RBF-FD stencils per Lagrangian point).
+void knn_point(const CellGrid& g, const double* xy, const Box& b, int64_t i, double dx, double dy, int n_l,
+               int64_t* id, double* d2, double* off) {
+    const double xi = xy[2 * i], yi = xy[2 * i + 1];
+    double qx = xi + dx, qy = yi + dy;
+    if (b.px) qx = b.x0 + std::fmod(std::fmod(qx - b.x0, b.lx) + b.lx, b.lx);
+    if (b.py) qy = b.y0 + std::fmod(std::fmod(qy - b.y0, b.ly) + b.ly, b.ly);
+    const int ci = g.cell_x(qx), cj = g.cell_y(qy);
+    int cnt = 0;
+    const int rmax = std::max(g.ncx, g.ncy) + 1;
+    const double cmin = std::min(g.cx, g.cy);
+    for (int r = 0; r <= rmax; ++r) {
+        for (int ddy = -r; ddy <= r; ++ddy) {
+            int yy = cj + ddy;
+            if (b.py) {
+                yy %= g.ncy;
+                if (yy < 0) yy += g.ncy;
+            } else if (yy < 0 || yy >= g.ncy) {
+                continue;
+            }
+            const bool edge_row = (ddy == -r || ddy == r);
+            for (int ddx = -r; ddx <= r; ddx += (edge_row ? 1 : 2 * r)) {
+                int xx = ci + ddx;
+                if (b.px) {
+                    xx %= g.ncx;
+                    if (xx < 0) xx += g.ncx;
+                } else if (xx < 0 || xx >= g.ncx) {
+                    if (r == 0) break;
+                    continue;
+                }
+                const int64_t c = (int64_t)yy * g.ncx + xx;
+                for (int64_t e = g.start[c]; e < g.start[c + 1]; ++e) {
+                    const int64_t j = g.items[e];
+                    const double ox = min_image(xy[2 * j] - xi, b.lx, b.px);
+                    const double oy = min_image(xy[2 * j + 1] - yi, b.ly, b.py);
+                    const double ex = ox - dx, ey = oy - dy;
+                    const double dd = ex * ex + ey * ey;
+                    if (cnt == n_l && (dd > d2[n_l - 1] || (dd == d2[n_l - 1] && j > id[n_l - 1]))) continue;
+                    bool dup = false;
+                    for (int m = 0; m < cnt; ++m)
+                        if (id[m] == j) { dup = true; break; }
+                    if (dup) continue;
+                    int pos = (cnt == n_l) ? n_l - 1 : cnt;
+                    while (pos > 0 && (d2[pos - 1] > dd || (d2[pos - 1] == dd && id[pos - 1] > j))) {
+                        d2[pos] = d2[pos - 1];
+                        id[pos] = id[pos - 1];
+                        off[2 * pos] = off[2 * pos - 2];
+                        off[2 * pos + 1] = off[2 * pos - 1];
+                        --pos;
+                    }
+                    d2[pos] = dd;
+                    id[pos] = j;
+                    off[2 * pos] = ox;
+                    off[2 * pos + 1] = oy;
+                    if (cnt < n_l) ++cnt;
+                }
+                if (r == 0) break;
+            }
+        }
+        if (cnt == n_l) {
+            const double reach = r * cmin;
+            if (d2[n_l - 1] < reach * reach) break;
+        }
+    }
+}
+
 // Quadratic WLS by Householder QR.  Returns 0, or 2 when cond(R)^2 > 1e12.
 int wls_qr(const double* off, int K, double s, double sigma_factor, double* M) {
     double rK = 0;
@@ -465,11 +533,16 @@ extern "C" mlbm_status mlbm_build_stencils(const mlbm_nodes* nodes, const mlbm_g
     return mlbm_build_stencils_ex(nodes, geo, K, s, sigma_factor, bb_mode, use_lagrange, MLBM_INTERP_WLS, out);
 }
 
-extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
-                                              double sigma_factor, int bb_mode, int use_lagrange, int interp,
-                                              mlbm_stencils** out) {
+namespace {
+
+// The builder.  K is the node's own stencil (least-squares fit, Lagrange
+// detection); for MLBM_INTERP_RBF_POINTS every interpolating direction gets
+// the n_l nearest nodes of its departure point and the node's device stencil
+// is their union, k_max slots wide.
+mlbm_status build_impl(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s, double sigma_factor,
+                       int bb_mode, int use_lagrange, int interp, int n_l, int k_max, mlbm_stencils** out) {
     clear_error();
-    if (interp != MLBM_INTERP_WLS && interp != MLBM_INTERP_RBF)
+    if (interp != MLBM_INTERP_WLS && interp != MLBM_INTERP_RBF && interp != MLBM_INTERP_RBF_POINTS)
         return set_error(MLBM_E_INVALID, "build_stencils: bad interpolant");
     if (!out) return set_error(MLBM_E_INVALID, "build_stencils: out is NULL");
     *out = nullptr;
@@ -479,6 +552,11 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
     if (n < 1 || n > (int64_t(1) << 31) - 1) return set_error(MLBM_E_INVALID, "build_stencils: bad node count");
     if (K < 6 || K > 32 || K % 4 != 0 || K > n)
         return set_error(MLBM_E_INVALID, "build_stencils: K must be a multiple of 4 in [8, 32] and <= n");
+    const bool points = interp == MLBM_INTERP_RBF_POINTS;
+    if (points && (n_l < 7 || n_l > 32 || n_l > n || k_max < K || k_max > 64 || k_max % 4 != 0))
+        return set_error(MLBM_E_INVALID,
+                         "build_stencils: n_l must be in [7, 32] and <= n, k_max a multiple of 4 in [K, 64]");
+    const int Kw = points ? k_max : K;  // device stencil width
     if (use_lagrange && K < 9) return set_error(MLBM_E_INVALID, "build_stencils: Lagrange needs K >= 9");
     if (!(s > 0) || !(sigma_factor > 0)) return set_error(MLBM_E_INVALID, "build_stencils: s and sigma must be > 0");
     if (bb_mode != MLBM_BB_SIMPLE && bb_mode != MLBM_BB_INTERPOLATED)
@@ -510,7 +588,7 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
     if (!st) return set_error(MLBM_E_OOM, "build_stencils: out of host memory");
     HostStencils& H = st->h;
     H.n = n;
-    H.K = K;
+    H.K = Kw;
     H.s = s;
     H.bb_mode = bb_mode;
     H.interp = interp;
@@ -518,11 +596,11 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
     const double* xy = nodes->xy;
     const CellGrid grid = make_grid(xy, n, b, K);
 
-    // caller-order work arrays
-    std::vector<int64_t> nid((size_t)n * K);
+    // caller-order work arrays (nid, Mc, Wc in the device stencil width Kw)
+    std::vector<int64_t> nid((size_t)n * Kw);
     std::vector<double> off((size_t)n * K * 2);
-    std::vector<double> Mc((size_t)n * 6 * K, 0.0);
-    std::vector<double> Wc(interp == MLBM_INTERP_RBF ? (size_t)n * 8 * K : 0, 0.0);
+    std::vector<double> Mc((size_t)n * 6 * Kw, 0.0);
+    std::vector<double> Wc(interp != MLBM_INTERP_WLS ? (size_t)n * 8 * Kw : 0, 0.0);
     std::vector<uint8_t> kind(n), center(n, 0);
     std::vector<double> lagh(n, 0.0), qc((size_t)n * 9, 0.0);
     std::vector<int8_t> slot((size_t)n * 9, 0);
@@ -531,10 +609,16 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
     int bad_code = 0;
 #pragma omp parallel
     {
-        std::vector<double> d2(K);
+        std::vector<double> d2(std::max(K, n_l)), pd2(std::max(n_l, 1)), poff(2 * std::max(n_l, 1)),
+            pw(std::max(n_l, 1)), Mown(6 * K);
+        std::vector<int64_t> own(K), pid(std::max(n_l, 1)), uni;
+        std::vector<std::vector<int64_t>> memb(9);
+        std::vector<std::vector<double>> wdir(9);
 #pragma omp for schedule(dynamic, 256)
         for (int64_t i = 0; i < n; ++i) {
-            knn_one(grid, xy, b, i, K, &nid[(size_t)i * K], d2.data(), &off[(size_t)i * K * 2]);
+            int64_t* nrow = &nid[(size_t)i * Kw];
+            knn_one(grid, xy, b, i, K, own.data(), d2.data(), &off[(size_t)i * K * 2]);
+            for (int j = 0; j < Kw; ++j) nrow[j] = j < K ? own[j] : i;  // padding: the node itself
             if (nodes->node_class[i] == MLBM_NODE_EQ) {
                 kind[i] = kKindEq;
                 continue;
@@ -554,11 +638,46 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
                 continue;
             }
             kind[i] = kKindWls;
-            code = wls_qr(&off[(size_t)i * K * 2], K, s, sigma_factor, &Mc[(size_t)i * 6 * K]);
+            code = wls_qr(&off[(size_t)i * K * 2], K, s, sigma_factor, Mown.data());
+            if (!points)
+                for (int a = 0; a < 6; ++a)
+                    for (int j = 0; j < K; ++j) Mc[((size_t)i * 6 + a) * Kw + j] = Mown[(size_t)a * K + j];
             if (!code && interp == MLBM_INTERP_RBF)
                 for (int k = 1; k < 9 && !code; ++k)
                     if (use[k])
                         code = rbf_weights(&off[(size_t)i * K * 2], K, dx[k], dy[k], &Wc[((size_t)i * 8 + k - 1) * K]);
+            if (!code && points) {
+                // the n_l nearest nodes of every departure point and their
+                // weights there; the device stencil is the union with the node
+                uni.assign(1, i);
+                for (int k = 1; k < 9 && !code; ++k) {
+                    memb[k].clear();
+                    if (!use[k]) continue;
+                    knn_point(grid, xy, b, i, dx[k], dy[k], n_l, pid.data(), pd2.data(), poff.data());
+                    code = rbf_weights(poff.data(), n_l, dx[k], dy[k], pw.data());
+                    memb[k].assign(pid.begin(), pid.begin() + n_l);
+                    wdir[k].assign(pw.begin(), pw.begin() + n_l);
+                    uni.insert(uni.end(), pid.begin(), pid.begin() + n_l);
+                }
+                if (!code) {
+                    std::sort(uni.begin(), uni.end());
+                    uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+                    if ((int)uni.size() > Kw) code = 9;
+                }
+                if (!code) {
+                    for (int j = 0; j < Kw; ++j) nrow[j] = j < (int)uni.size() ? uni[j] : i;
+                    for (int k = 1; k < 9; ++k) {
+                        double* row = &Wc[((size_t)i * 8 + k - 1) * Kw];
+                        if (!use[k]) {  // simple bounce-back: the kernel copies the node's own value
+                            continue;
+                        }
+                        for (int m = 0; m < n_l; ++m) {
+                            const int u = (int)(std::lower_bound(uni.begin(), uni.end(), memb[k][m]) - uni.begin());
+                            row[u] = wdir[k][m];
+                        }
+                    }
+                }
+            }
             if (code) {
 #pragma omp critical
                 { if (bad_node < 0 || i < bad_node) { bad_node = i; bad_code = code; } }
@@ -569,6 +688,9 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
         delete st;
         if (bad_code == 8)
             return set_error(MLBM_E_GEOMETRY, "build_stencils: node " + std::to_string(bad_node) + " lies inside a solid");
+        if (bad_code == 9)
+            return set_error(MLBM_E_INVALID, "build_stencils: the departure stencils of node " +
+                                                 std::to_string(bad_node) + " hold more than k_max nodes");
         return set_error(MLBM_E_SINGULAR_STENCIL,
                          "build_stencils: degenerate least-squares stencil at node " + std::to_string(bad_node));
     }
@@ -584,9 +706,9 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
     H.inv.resize(n);
     for (int64_t p = 0; p < n; ++p) H.inv[H.perm[p]] = p;
 
-    H.idx.resize((size_t)n * K);
-    H.M.assign((size_t)n * 6 * K, 0.0);
-    H.Wr.assign(interp == MLBM_INTERP_RBF ? (size_t)n * 8 * K : 0, 0.0);
+    H.idx.resize((size_t)n * Kw);
+    H.M.assign((size_t)n * 6 * Kw, 0.0);
+    H.Wr.assign(interp != MLBM_INTERP_WLS ? (size_t)n * 8 * Kw : 0, 0.0);
     H.kind.resize(n);
     H.center.resize(n);
     H.lag_h.resize(n);
@@ -598,13 +720,13 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
     mlbm_stencil_info& I = H.info;
     I = mlbm_stencil_info{};
     I.n = n;
-    I.K = K;
+    I.K = Kw;
     I.s = s;
     for (int64_t p = 0; p < n; ++p) {
         const int64_t i = H.perm[p];
-        for (int j = 0; j < K; ++j) H.idx[(size_t)p * K + j] = (int32_t)H.inv[nid[(size_t)i * K + j]];
-        std::memcpy(&H.M[(size_t)p * 6 * K], &Mc[(size_t)i * 6 * K], sizeof(double) * 6 * K);
-        if (!Wc.empty()) std::memcpy(&H.Wr[(size_t)p * 8 * K], &Wc[(size_t)i * 8 * K], sizeof(double) * 8 * K);
+        for (int j = 0; j < Kw; ++j) H.idx[(size_t)p * Kw + j] = (int32_t)H.inv[nid[(size_t)i * Kw + j]];
+        std::memcpy(&H.M[(size_t)p * 6 * Kw], &Mc[(size_t)i * 6 * Kw], sizeof(double) * 6 * Kw);
+        if (!Wc.empty()) std::memcpy(&H.Wr[(size_t)p * 8 * Kw], &Wc[(size_t)i * 8 * Kw], sizeof(double) * 8 * Kw);
         H.kind[p] = kind[i];
         H.center[p] = center[i];
         H.lag_h[p] = lagh[i];
@@ -625,6 +747,24 @@ extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlb
     I.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = st;
     return MLBM_OK;
+}
+
+}  // namespace
+
+extern "C" mlbm_status mlbm_build_stencils_ex(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K, double s,
+                                              double sigma_factor, int bb_mode, int use_lagrange, int interp,
+                                              mlbm_stencils** out) {
+    if (interp == MLBM_INTERP_RBF_POINTS)
+        return set_error(MLBM_E_INVALID, "build_stencils_ex: stencils per departure point need "
+                                         "mlbm_build_stencils_points");
+    return build_impl(nodes, geo, K, s, sigma_factor, bb_mode, use_lagrange, interp, 0, K, out);
+}
+
+extern "C" mlbm_status mlbm_build_stencils_points(const mlbm_nodes* nodes, const mlbm_geometry* geo, int n_l,
+                                                  int k_max, double s, int bb_mode, int use_lagrange,
+                                                  mlbm_stencils** out) {
+    return build_impl(nodes, geo, 16, s, 0.7071067811865476, bb_mode, use_lagrange, MLBM_INTERP_RBF_POINTS, n_l,
+                      k_max, out);
 }
 
 extern "C" void mlbm_stencils_free(mlbm_stencils* st) { delete st; }
@@ -705,7 +845,7 @@ extern "C" int mlbm_stencils_order(const mlbm_stencils* st) { return st ? st->h.
 extern "C" mlbm_status mlbm_stencils_export_weights(const mlbm_stencils* st, double* W) {
     if (!st || !W) return set_error(MLBM_E_INVALID, "stencils_export_weights: NULL argument");
     const HostStencils& H = st->h;
-    if (H.interp != MLBM_INTERP_RBF) return set_error(MLBM_E_INVALID, "stencils_export_weights: not RBF-FD stencils");
+    if (H.interp == MLBM_INTERP_WLS) return set_error(MLBM_E_INVALID, "stencils_export_weights: not RBF-FD stencils");
     const int K = H.K;
     for (int64_t p = 0; p < H.n; ++p) {
         const int64_t i = H.perm[p];

@@ -16,7 +16,7 @@ import numpy as np
 from . import _build
 
 MODEL_BGK, MODEL_TAU1 = 0, 1
-INTERP_WLS, INTERP_RBF = 0, 1
+INTERP_WLS, INTERP_RBF, INTERP_RBF_POINTS = 0, 1, 2
 ORDER_HILBERT, ORDER_MORTON, ORDER_ROWS, ORDER_INPUT = 0, 1, 2, 3
 BB_SIMPLE, BB_INTERPOLATED = 0, 1
 NODE_FLUID, NODE_WALL, NODE_EQ = 0, 1, 2
@@ -66,6 +66,7 @@ def lib():
             sig = {
                 "mlbm_build_stencils": (st, [_vp, _vp, _i32, _dbl, _dbl, _i32, _i32, _vp]),
                 "mlbm_build_stencils_ex": (st, [_vp, _vp, _i32, _dbl, _dbl, _i32, _i32, _i32, _vp]),
+                "mlbm_build_stencils_points": (st, [_vp, _vp, _i32, _i32, _dbl, _i32, _i32, _vp]),
                 "mlbm_stencils_export_weights": (st, [_vp, _vp]),
                 "mlbm_stencils_free": (None, [_vp]),
                 "mlbm_stencils_info": (st, [_vp, _vp]),
@@ -94,6 +95,7 @@ def lib():
                 "mlbm_last_step_ms": (_dbl, [_vp]),
                 "mlbm_set_kernel_variant": (st, [_vp, _i32]),
                 "mlbm_kernel_variant": (_i32, [_vp]),
+                "mlbm_autotune_times": (_i32, [_vp, _vp, _i32]),
                 "mlbm_autotune": (st, [_vp, _i32, _vp]),
                 "mlbm_autotune_ex": (st, [_vp, _i32, _i32, _vp]),
                 "mlbm_batch_init": (st, [_vp, _vp, _vp, _i32]),
@@ -187,7 +189,7 @@ class Stencils:
 
 def build_stencils(xy, node_class, box, sides, disks=None, eq_values=None, area=None, K=16, s=1.0,
                    sigma_factor=0.7071067811865476, bb_mode=BB_INTERPOLATED, use_lagrange=True,
-                   interp=INTERP_WLS) -> Stencils:
+                   interp=INTERP_WLS, n_l=25) -> Stencils:
     xy = _f64(xy)
     n = xy.shape[0]
     cls = np.ascontiguousarray(node_class, dtype=np.uint8)
@@ -198,9 +200,14 @@ def build_stencils(xy, node_class, box, sides, disks=None, eq_values=None, area=
     geo = _Geometry(float(box[0]), float(box[1]), float(box[2]), float(box[3]), (_i32 * 4)(*[int(v) for v in sides]),
                     len(dk), _ptr(dk) if len(dk) else None)
     h = _vp()
-    _check(lib().mlbm_build_stencils_ex(ctypes.byref(nodes), ctypes.byref(geo), int(K), float(s),
-                                        float(sigma_factor), int(bb_mode), int(bool(use_lagrange)), int(interp),
-                                        ctypes.byref(h)))
+    if interp == INTERP_RBF_POINTS:
+        # K is the union width k_max; the departure stencils hold n_l nodes
+        _check(lib().mlbm_build_stencils_points(ctypes.byref(nodes), ctypes.byref(geo), int(n_l), int(K), float(s),
+                                                int(bb_mode), int(bool(use_lagrange)), ctypes.byref(h)))
+    else:
+        _check(lib().mlbm_build_stencils_ex(ctypes.byref(nodes), ctypes.byref(geo), int(K), float(s),
+                                            float(sigma_factor), int(bb_mode), int(bool(use_lagrange)), int(interp),
+                                            ctypes.byref(h)))
     return Stencils(h, n, int(K), None)
 
 
@@ -422,6 +429,13 @@ def autotune(ctx: Context, steps_per_variant: int = 20, flush_l2: bool = False) 
     ms = ctypes.c_double()
     _check(lib().mlbm_autotune_ex(ctx.handle, int(steps_per_variant), int(bool(flush_l2)), ctypes.byref(ms)))
     return kernel_variant(ctx), ms.value
+
+
+def autotune_times(ctx: Context) -> dict:
+    """ms per step of every variant timed by the last autotune {variant: ms}."""
+    ms = np.full(64, -1.0)
+    n = lib().mlbm_autotune_times(ctx.handle, _ptr(ms), 64)
+    return {v: float(ms[v]) for v in range(max(n, 0)) if ms[v] >= 0}
 
 
 def batch_init(stencils: list, params: list) -> Context:

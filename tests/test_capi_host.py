@@ -101,6 +101,24 @@ def test_builder_errors():
     assert e.value.status == 8
 
 
+def test_builder_rejects_too_few_and_no_nodes():
+    """Fewer nodes than the stencil size, and an empty node set, are
+    MLBM_E_INVALID before any work; one partition per node is a valid split
+    of a small set, more partitions than nodes is not."""
+    xy = I.lattice(3, 3).xy
+    with pytest.raises(mlbm.MlbmError) as e:
+        mlbm.build_stencils(xy, np.zeros(9, np.uint8), (0, 0, 3, 3), (0, 0, 0, 0), K=12)
+    assert e.value.status == 1
+    with pytest.raises((mlbm.MlbmError, ValueError)) as e:
+        mlbm.build_stencils(np.zeros((0, 2)), np.zeros(0, np.uint8), (0, 0, 3, 3), (0, 0, 0, 0), K=12)
+    w = I.lattice(5, 5)
+    st = mlbm.build_stencils_for(w, K=12, s=1.0)
+    plan = mlbm.partition_plan(st, 25)
+    assert np.all(plan["n_owned"] == 1) and np.all(plan["n_halo"] == 11)
+    with pytest.raises(mlbm.MlbmError):
+        mlbm.partition_plan(st, 26)
+
+
 @pytest.mark.parametrize("order", [1, 2, 3, 0])
 def test_reordering_keeps_the_stencils(order):
     """Re-ordering the device node order changes no stencil datum in the
@@ -143,6 +161,33 @@ def test_builder_rbf_weights_match_oracle(case):
         interp_k = sel & ~((op.link[:, k] != 0) & (bb == 0))
         err = np.abs(W[interp_k, k] - op.W[interp_k, k]).max()
         assert err < 1e-8, (k, err)
+
+
+@pytest.mark.parametrize("case", ["porous", "karman", "jittered"])
+def test_builder_points_stencils_match_oracle(case):
+    """RBF-FD stencils per Lagrangian point (Sec. 2.2, N_L = 25): the host
+    builder's union stencils (grid search around each departure point) are
+    the oracle's (brute force) node for node, and every direction's weights
+    agree to FP64 round-off; a k_max below the union is rejected."""
+    if case == "porous":
+        w, s, bb = I.porous(seed=10, n_target=3000, porosity=0.7), 1.0, 1
+    elif case == "karman":
+        w, s, bb = I.karman(seed=2, scale=0.25), 0.5, 0
+    else:
+        w, s, bb = I.jittered_periodic(24, 20, 0.25, seed=7), 0.8, 1
+    st = mlbm.build_stencils_for(w, K=64, s=s, bb_mode=bb, interp=mlbm.INTERP_RBF_POINTS, n_l=25)
+    ex = mlbm.stencils_export(st)
+    W = mlbm.stencils_export_weights(st)
+    op = O.Operator(w, K=16, s=s, bb_mode=bb, interp="rbf_points", n_l=25, k_max=64).check()
+    assert np.array_equal(ex["kind"], op.kind)
+    sel = op.kind == 0
+    assert np.array_equal(ex["idx"][sel], op.idx[sel])          # same union, same slot order
+    for k in range(1, 9):
+        rows = sel & ~((op.link[:, k] != 0) & (bb == 0))
+        assert np.abs(W[rows, k] - op.W[rows, k]).max() < 1e-10, k
+    with pytest.raises(mlbm.MlbmError) as e:
+        mlbm.build_stencils_for(w, K=28, s=s, bb_mode=bb, interp=mlbm.INTERP_RBF_POINTS, n_l=25)
+    assert e.value.status == 1
 
 
 def test_context_calls_reject_null_arguments_without_a_device():

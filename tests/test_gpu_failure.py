@@ -20,7 +20,7 @@ from paper_2312_14789_gb300 import mlbm
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("variant", [4, 7])
+@pytest.mark.parametrize("variant", [4, 7, 27, 28])
 @pytest.mark.parametrize("model", ["bgk", "tau1"])
 def test_withheld_copy_times_out_and_context_recovers(model, variant):
     w = I.porous(seed=47, n_target=20000, porosity=0.7)

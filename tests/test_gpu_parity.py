@@ -48,7 +48,7 @@ def gpu_ctx(w, K, s, bb_mode, params, sigma=0.7071067811865476, use_lagrange=Tru
     return ctx
 
 
-VARIANTS = list(range(27))
+VARIANTS = list(range(30))
 
 
 # ----------------------------------------------------------------- plain MLBM
@@ -135,6 +135,54 @@ def test_rbf_steps_match_oracle_elementwise(case, variant):
     fx, fy, _, _ = mlbm.drag_lift(ctx, 1.0, 1.0)
     ox, oy = O.force_bgk(op, mlbm.get_populations(ctx))
     assert abs(fx - ox) <= 1e-4 * max(abs(ox), 1e-12) + 1e-9 and abs(fy - oy) <= 1e-4 * max(abs(ox), 1e-12) + 1e-9
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("case", ["jittered", "karman_small", "porous_small", "porous_tau1"])
+def test_rbf_points_steps_match_oracle_elementwise(case, variant):
+    """RBF-FD with a stencil per Lagrangian point (Sec. 2.2, N_L = 25 nearest
+    nodes of every departure point; union stencils 64 wide): the GPU step
+    against the oracle's step with its own stencils and weights, 10 steps
+    from a random state, BGK and tau = 1."""
+    model = mlbm.MODEL_BGK
+    if case == "jittered":
+        w, s, bb, tau, g = I.jittered_periodic(37, 29, 0.25, seed=4), 0.8, 1, 0.75, (1e-5, 3e-6)
+    elif case == "karman_small":
+        w, s, bb, tau, g = I.karman(seed=2, scale=0.25), 0.5, 0, 0.62, (0.0, 0.0)
+    elif case == "porous_small":
+        w, s, bb, tau, g = I.porous(seed=5, n_target=8000), 1.0, 1, 0.8, (1e-5, 0.0)
+    else:
+        w, s, bb, tau, g = I.porous(seed=6, n_target=8000), 1.0, 1, 1.0, (1e-5, 0.0)
+        model = mlbm.MODEL_TAU1
+    st = mlbm.build_stencils_for(w, K=64, s=s, bb_mode=bb, interp=mlbm.INTERP_RBF_POINTS, n_l=25)
+    ctx = mlbm.init(st, mlbm.Params(model, tau, 0.0, *g))
+    mlbm.set_kernel_variant(ctx, variant)
+    op = O.Operator(w, K=16, s=s, bb_mode=bb, interp="rbf_points", n_l=25, k_max=64).check()
+    if model == mlbm.MODEL_BGK:
+        f0 = to_f32_state(random_populations(w.n, 11))
+        mlbm.set_populations(ctx, f0)
+        f, done = f0, 0
+        for n_steps in (1, 9):
+            mlbm.step(ctx, n_steps)
+            for _ in range(n_steps):
+                f = O.bgk_step(op, f, tau, g)
+            done += n_steps
+            err = np.abs(mlbm.get_populations(ctx) - f).max()
+            assert err < pop_tol(done), (case, done, err)
+    else:
+        rng = np.random.default_rng(12)
+        ru = np.column_stack([1 + 0.01 * rng.standard_normal(w.n), 0.01 * rng.standard_normal(w.n),
+                              0.01 * rng.standard_normal(w.n)])
+        ru = ru.astype(np.float32).astype(np.float64)
+        mlbm.set_fields(ctx, ru)
+        r, done = mlbm.get_fields(ctx), 0
+        for n_steps in (1, 9):
+            mlbm.step(ctx, n_steps)
+            for _ in range(n_steps):
+                r = O.mlbm1_step(op, r, g)
+            done += n_steps
+            err = np.abs(mlbm.get_fields(ctx) - r).max()
+            assert err < 5 * pop_tol(done), (case, done, err)
 
 
 def test_rbf_poiseuille_2000_steps_matches_oracle():

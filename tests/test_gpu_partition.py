@@ -41,7 +41,7 @@ def _initial(w, model, seed):
 
 
 @pytest.mark.parametrize("n_parts,variant,bounds", [(2, 26, None), (3, 11, None), (5, 4, None), (4, 25, "uneven"),
-                                                    (2, 7, "uneven"), (1, 12, None)])
+                                                    (2, 7, "uneven"), (1, 12, None), (3, 27, None)])
 @pytest.mark.parametrize("name", ["porous_tau1", "porous_bgk", "karman_hybrid_bgk"])
 def test_partitioned_step_is_bitwise_the_unpartitioned(name, n_parts, variant, bounds):
     w, s, bb, p = _case(name)
