@@ -65,6 +65,9 @@ CASES = [(re, s) for re in (100, 200) for s in (0.5, 0.25, 0.125)]
 # time-to-steady legs (criterion of the learned warm-start configuration)
 TOL, WINDOW, CHECK = 1e-7, 1000, 100
 PAPER_THRESHOLD, PAPER_DN, PAPER_CHECK = 1e-2, 20000, 1000
+# nodes per timed oracle step: the oracle runs node sets of 16384 or more on
+# all host threads (smaller ones on one)
+ORACLE_SAMPLE = 32768
 
 
 def tau_of(re, s):
@@ -108,10 +111,13 @@ def measured_traffic(workload, variant, order=0, node_updates=None):
         rec = json.load(open(TRAFFIC[workload]))
     except (OSError, KeyError, ValueError):
         return None
-    if rec.get("kernel_source_hash") != kernel_source_hash() or rec.get("kernel_variant") != variant \
-            or rec.get("node_order", "hilbert") != ORDER_NAMES[order]:
+    if rec.get("kernel_source_hash") != kernel_source_hash() or rec.get("node_order", "hilbert") != ORDER_NAMES[order]:
         return None
-    t = float(rec["dram_bytes_per_launch"])
+    by_variant = rec.get("dram_bytes_per_launch_by_variant") or {str(rec.get("kernel_variant")): rec.get(
+        "dram_bytes_per_launch")}
+    if str(variant) not in by_variant:
+        return None
+    t = float(by_variant[str(variant)])
     if node_updates and rec.get("node_updates_per_launch"):
         t *= node_updates / float(rec["node_updates_per_launch"])
     return t
@@ -279,8 +285,9 @@ def run_reference(args, rank, world):
         n = inputs["karman"].n * len(CASES)
     else:
         n = sum(w.n for w in inputs["batch"])
-    oracle_sample_rate(args, inputs, 4096, 0, reps=args.warmup)              # untimed warm-up steps
-    value, threads, desc, per = oracle_sample_rate(args, inputs, 4096, 0, reps=args.steps)
+    # a sample large enough for the oracle to use every host core
+    oracle_sample_rate(args, inputs, ORACLE_SAMPLE, 0, reps=args.warmup)     # untimed warm-up steps
+    value, threads, desc, per = oracle_sample_rate(args, inputs, ORACLE_SAMPLE, 0, reps=args.steps)
     total = sum(per)
     cfg = workload_config(args, inputs, None, n, 1)
     print(json.dumps({
@@ -550,7 +557,8 @@ def run_ours(args, rank, world, local_rank):
     avg_ms = my_ms / args.steps
     achieved = bytes_launch / (avg_ms / 1e3) / 1e9
     traffic = measured_traffic(args.workload, variant, order, n)
-    cpu_val, cpu_threads, cpu_desc, _ = oracle_sample_rate(args, inputs, 8192, 1, min_seconds=10.0, max_reps=20000)
+    cpu_val, cpu_threads, cpu_desc, _ = oracle_sample_rate(args, inputs, ORACLE_SAMPLE, 1, min_seconds=10.0,
+                                                           max_reps=20000)
     cfg = dict(workload_config(args, inputs, infos, n, world), parallelism=(
         f"{world} ranks x own samples (weak)" if args.scaling == "weak" else f"{args.samples} samples split over "
         f"{world} ranks (strong)"), kernel_variant=variant, node_order=ORDER_NAMES[order],

@@ -93,6 +93,7 @@ struct mlbm_ctx {
 
 namespace {
 constexpr int kGraphSteps = 16;
+constexpr int kMaxK = 64;  // widest device stencil (RBF-FD unions per Lagrangian point)
 constexpr int kMaxVariant = 29;  // step kernel variants 0..29 (see mlbm_set_kernel_variant)
 }
 
@@ -226,6 +227,8 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     c->box_area = H.box_area;
     c->n_pad = (H.n + 127) / 128 * 128;
     const int64_t n = H.n, np = c->n_pad;
+    if (H.K < 4 || H.K > kMaxK || H.K % 4 != 0)
+        return set_error(MLBM_E_INVALID, "init: stencil width must be a multiple of 4 in [4, 64]");
     // state slots: the nodes, then the halo copies of a partition's neighbours
     c->n_halo = H.n_halo;
     const int64_t nps = (H.n + H.n_halo + 127) / 128 * 128;
@@ -253,7 +256,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
             // stencil slots in increasing node position: lanes of a warp that
             // gather slot j of consecutive (Hilbert-ordered) nodes then touch
             // nearby addresses; the matrix columns follow the same order
-            int order[32];
+            int order[kMaxK];
             for (int j = 0; j < K; ++j) order[j] = j;
             if (H.slot_key.empty())
                 std::sort(order, order + K,
