@@ -91,7 +91,8 @@ def algorithmic_bytes(info, K, model="bgk"):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels_bgk.cu", "kernels_tau1.cu", "kernels_rbf.cu", "kernels_ring1.cu",
+    for f in ("kernels.cu", "kernels_bgk.cu", "kernels_bgk_generic.cu", "kernels_bgk_alt.cu", "kernels_tau1.cu",
+              "kernels_rbf.cu", "kernels_ring1.cu",
               "kernels_tma.cu", "step_node.cuh", "ring.cuh", "launch_util.cuh", "device_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2312_14789_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]

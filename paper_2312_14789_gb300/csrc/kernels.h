@@ -18,6 +18,12 @@ cudaError_t launch_wall_traction(const dev::Stencil& S, int model, const float4*
                                  const double* nrm, const double* ds, int m, double* out, cudaStream_t st);
 // raises the dynamic shared-memory limit of the staged step kernel (variant 22)
 cudaError_t prepare_staged_step(int Kq, int stage_max);
+// BGK variants 0-3 (kernels_bgk_generic.cu)
+cudaError_t launch_bgk_step_generic(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,
+                                    float* f0out, const dev::Collide& C, int variant, cudaStream_t st);
+// BGK variants 14-19 and 22 (kernels_bgk_alt.cu)
+cudaError_t launch_bgk_step_alt(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,
+                                float* f0out, const dev::Collide& C, int variant, cudaStream_t st);
 // RBF-FD stencils (kernels_rbf.cu); launch_bgk_step / launch_tau1_step hand
 // contexts with per-direction weights to these
 cudaError_t launch_bgk_step_rbf(const dev::Stencil& S, const float4* f8in, const float* f0in, float4* f8out,

@@ -595,5 +595,52 @@ __device__ __forceinline__ void tau1_node(const Stencil& S, const float4* __rest
     }
 }
 
+// ---- BGK step grids (instantiated in kernels_bgk.cu and kernels_bgk_generic.cu)
+template <int KQ, int LPN, int MINB, bool SPEC = false, int BS = 256, bool PDL = false>
+__global__ void __launch_bounds__(BS, MINB) bgk_step_kernel(Stencil S, const float4* __restrict__ f8in,
+                                                             const float* __restrict__ f0in,
+                                                             float4* __restrict__ f8out, float* __restrict__ f0out,
+                                                             Collide C) {
+    if (PDL) {
+        if (threadIdx.x < 32) prefetch_tile<KQ>(S, blockIdx.x * (BS / LPN), BS / LPN, threadIdx.x & 31u);
+        pdl_trigger();
+        pdl_wait();
+    }
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = tid / LPN;
+    const int h = tid % LPN;
+    if (p >= S.n) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
+    bgk_node<KQ, LPN, true, false, SPEC>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
+}
+
+// Persistent form: gridDim.x resident blocks walk the node tiles; before a
+// tile, warp 0 prefetches the stencil rows of the tile `dist` rounds ahead
+// into L2, so the streamed loads of later tiles hit L2 instead of waiting on
+// HBM while this tile gathers and collides.
+template <int KQ, int LPN, int MINB, bool SPEC = false, int BS = 256, bool PDL = false>
+__global__ void __launch_bounds__(BS, MINB) bgk_step_persistent(Stencil S, const float4* __restrict__ f8in,
+                                                                const float* __restrict__ f0in,
+                                                                float4* __restrict__ f8out,
+                                                                float* __restrict__ f0out, Collide C, int dist) {
+    constexpr int TN = BS / LPN;
+    const int n_tiles = (S.n + TN - 1) / TN;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = LPN == 1 ? (1u << lane) : (3u << (lane & ~1u));
+    const int h = threadIdx.x % LPN;
+    if (threadIdx.x < 32)
+        for (int d = 0; d < dist; ++d) prefetch_tile<KQ>(S, (blockIdx.x + d * gridDim.x) * TN, TN, lane);
+    if (PDL) {
+        pdl_trigger();
+        pdl_wait();
+    }
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (threadIdx.x < 32) prefetch_tile<KQ>(S, (tile + dist * gridDim.x) * TN, TN, lane);
+        const int p = tile * TN + threadIdx.x / LPN;
+        if (p < S.n) bgk_node<KQ, LPN, true, false, SPEC>(S, f8in, f0in, f8out, f0out, C, p, h, grp);
+    }
+}
+
 }  // namespace dev
 }  // namespace mlbm
