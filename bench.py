@@ -197,7 +197,8 @@ def make_inputs(args, rank, world):
     if args.workload == "karman_sweep":
         return {"karman": I.karman(seed=2)}
     specs, assignment = porous_specs(args, rank, world)
-    out = {"specs": specs, "assignment": assignment, "batch": I.generate(specs)}
+    procs = min(16, int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), len(specs))
+    out = {"specs": specs, "assignment": assignment, "batch": I.generate(specs, procs=procs)}
     if rank == 0 and world == 1 and args.steady:
         test = [{"seed": 20000 + i, "n_target": 200_000, "porosity": 0.7} for i in range(args.steady_samples)]
         train = [{"seed": 10000 + i, "n_target": args.train_nodes, "porosity": 0.7}
@@ -450,8 +451,20 @@ def steady_legs(inputs, log):
     return out
 
 
+def share_host_cores(world):
+    """Ranks on one node split the host cores between them (stencil builds
+    and the oracle use OpenMP; node generation uses worker processes);
+    must run before torch or the library is loaded."""
+    local = int(os.environ.get("LOCAL_WORLD_SIZE", world))
+    per = max(1, (os.cpu_count() or 1) // max(local, 1))
+    if local > 1 and "OMP_NUM_THREADS" not in os.environ:
+        os.environ["OMP_NUM_THREADS"] = str(per)
+    return per
+
+
 def run_ours(args, rank, world, local_rank):
     t_setup0 = time.perf_counter()
+    share_host_cores(world)
     inputs = make_inputs(args, rank, world)      # worker processes, before CUDA is touched
     t_gen = time.perf_counter() - t_setup0
     import torch

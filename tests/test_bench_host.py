@@ -83,3 +83,18 @@ def test_porous_batch_specs():
     # seeds decide the samples: a later rank's set continues the sequence
     b = I.porous_batch_specs(4, first_seed=1002)
     assert b[0]["n_target"] == a[2]["n_target"] and b[0]["porosity"] == a[2]["porosity"]
+
+
+def test_ranks_share_the_host_cores(monkeypatch):
+    monkeypatch.delenv("OMP_NUM_THREADS", raising=False)
+    monkeypatch.setenv("LOCAL_WORLD_SIZE", "4")
+    monkeypatch.setattr(bench.os, "cpu_count", lambda: 64)
+    assert bench.share_host_cores(4) == 16
+    assert bench.os.environ["OMP_NUM_THREADS"] == "16"
+    monkeypatch.setenv("OMP_NUM_THREADS", "3")          # a caller's setting stays
+    bench.share_host_cores(4)
+    assert bench.os.environ["OMP_NUM_THREADS"] == "3"
+    monkeypatch.delenv("OMP_NUM_THREADS")
+    monkeypatch.setenv("LOCAL_WORLD_SIZE", "1")
+    bench.share_host_cores(1)
+    assert "OMP_NUM_THREADS" not in bench.os.environ
