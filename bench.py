@@ -27,6 +27,12 @@ velocity over 2e4 steps per unit time below 1e-2) on the cold batch.
 40 spacings, ~260k nodes, BGK, simple bounce-back; the six runs Re in
 {100, 200} x s in {1/2, 1/4, 1/8} in one batched context).
 
+`--workload porous_box`: one porous sample of Sec. 3.2 at full size (seed 3,
+~960k nodes, porosity 0.7, K = 16, tau = 1, interpolated bounce-back, s = 1/2,
+g = 1e-5 along x); ~450 MB of stencil rows per step, larger than L2, so
+steps are timed back to back.  Under torchrun every rank steps its own box
+(seed 3 + rank).
+
 Arms:
   default            the CUDA path through the C ABI (device-resident state)
   --impl reference   the FP64 CPU oracle on a bounded node sample of the
@@ -61,6 +67,8 @@ ORDER_NAMES = ["hilbert", "morton", "rows", "input"]
 # vortex-street sweep
 U0, D = 0.05, 40.0
 CASES = [(re, s) for re in (100, 200) for s in (0.5, 0.25, 0.125)]
+# single porous box
+BOX_SEED, BOX_S, BOX_G = 3, 0.5, 1e-5
 
 # time-to-steady legs (criterion of the learned warm-start configuration)
 TOL, WINDOW, CHECK = 1e-7, 1000, 100
@@ -99,7 +107,8 @@ def kernel_source_hash():
 
 
 TRAFFIC = {"porous_batch": os.path.join(ROOT, "profiles", "tau1_step_porous_batch.json"),
-           "karman_sweep": os.path.join(ROOT, "profiles", "bgk_step_karman_sweep.json")}
+           "karman_sweep": os.path.join(ROOT, "profiles", "bgk_step_karman_sweep.json"),
+           "porous_box": os.path.join(ROOT, "profiles", "tau1_step_porous_box.json")}
 
 
 def measured_traffic(workload, variant, order=0, node_updates=None):
@@ -196,6 +205,8 @@ def make_inputs(args, rank, world):
     from paper_2312_14789_gb300 import inputs as I
     if args.workload == "karman_sweep":
         return {"karman": I.karman(seed=2)}
+    if args.workload == "porous_box":
+        return {"box": I.porous(seed=BOX_SEED + rank)}
     specs, assignment = porous_specs(args, rank, world)
     procs = min(16, int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), len(specs))
     out = {"specs": specs, "assignment": assignment, "batch": I.generate(specs, procs=procs)}
@@ -218,6 +229,9 @@ def build_batch(args, inputs):
         sts = [st_by_s[s] for _, s in CASES]
         params = [mlbm.Params(mlbm.MODEL_BGK, tau_of(re, s), 0.0, 0.0, 0.0) for re, s in CASES]
         return sts, params, "bgk", list(st_by_s.values())
+    if args.workload == "porous_box":
+        st = mlbm.build_stencils_for(inputs["box"], K=16, s=BOX_S, bb_mode=mlbm.BB_INTERPOLATED)
+        return [st], [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, BOX_G, 0.0)], "tau1", [st]
     sts = [mlbm.build_stencils_for(w, K=16, s=sp["s"], bb_mode=mlbm.BB_INTERPOLATED)
            for w, sp in zip(inputs["batch"], inputs["specs"])]
     params = [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, sp["g"], 0.0) for sp in inputs["specs"]]
@@ -232,6 +246,12 @@ def workload_config(args, inputs, infos, n, world):
                 "nodes_per_run": w.n, "K": 16, "model": "BGK", "D_spacings": 40, "U0": U0, "seed": 2,
                 "bounce_back": "simple", "node_updates_per_step": n,
                 "l2": "working set ~780 MB > L2 (129 MB): steps timed back to back, no flush"}
+    if args.workload == "porous_box":
+        w = inputs["box"]
+        return {"workload": "porous_box", "seed": BOX_SEED, "nodes": w.n, "porosity": round(w.meta["porosity"], 4),
+                "s": BOX_S, "g": BOX_G, "K": 16, "model": "MLBM1 (tau = 1)", "bounce_back": "interpolated",
+                "node_updates_per_step": n,
+                "l2": "working set ~480 MB > L2 (129 MB): steps timed back to back, no flush"}
     ws = inputs["batch"]
     return {"workload": "porous_batch_64" if args.samples == 64 else f"porous_batch_{args.samples}",
             "samples_per_rank": len(ws), "seeds": [sp["seed"] for sp in inputs["specs"]][:1] +
@@ -256,6 +276,9 @@ def oracle_sample_rate(args, inputs, n_sample, seed, min_seconds=0.0, max_reps=1
     if args.workload == "karman_sweep":
         w, s, model = inputs["karman"], 0.5, "bgk"
         what = f"the {w.n}-node vortex-street node set (Re = 100, s = 1/2)"
+    elif args.workload == "porous_box":
+        w, s, model = inputs["box"], BOX_S, "tau1"
+        what = f"the porous box (seed {BOX_SEED}, {w.n} nodes, s = {BOX_S})"
     else:
         i = int(np.argsort([w.n for w in inputs["batch"]])[len(inputs["batch"]) // 2])
         w, s, model = inputs["batch"][i], inputs["specs"][i]["s"], "tau1"
@@ -285,6 +308,8 @@ def run_reference(args, rank, world):
     inputs = make_inputs(argparse.Namespace(**{**vars(args), "steady": False}), 0, 1)
     if args.workload == "karman_sweep":
         n = inputs["karman"].n * len(CASES)
+    elif args.workload == "porous_box":
+        n = inputs["box"].n
     else:
         n = sum(w.n for w in inputs["batch"])
     # a sample large enough for the oracle to use every host core
@@ -608,7 +633,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="porous_batch", choices=["porous_batch", "karman_sweep"])
+    ap.add_argument("--workload", default="porous_batch", choices=["porous_batch", "karman_sweep", "porous_box"])
     ap.add_argument("--samples", type=int, default=64, help="porous samples per batch (64: the configuration)")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"])
     ap.add_argument("--variant", type=int, default=-1,
