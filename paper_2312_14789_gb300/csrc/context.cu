@@ -243,6 +243,15 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
     std::vector<int> hslot(np, -1), hperm(np, 0), hlinknodes;
     std::vector<dev::LinkRec> hlinks;
     std::vector<float4> heqv(np, make_float4(0, 0, 0, 0));
+    // link records in node order: their slots first, then every node's rows
+    // in parallel (each node writes only its own positions)
+    for (int64_t q = 0; q < n; ++q)
+        if (H.link_mask[q]) {
+            hslot[q] = (int)hlinknodes.size();
+            hlinknodes.push_back((int)q);
+        }
+    hlinks.resize(hlinknodes.size());
+#pragma omp parallel for schedule(static, 4096)
     for (int64_t q = 0; q < n; ++q) {
         const uint8_t kind = H.kind[q];
         const uint16_t lm = H.link_mask[q];
@@ -293,9 +302,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
             dev::LinkRec r{};
             r.mask = lm;
             for (int k = 1; k < 9; ++k) r.t[k - 1] = (float)(1.0 - 2.0 * H.q[(size_t)q * 9 + k]);
-            hslot[q] = (int)hlinks.size();
-            hlinks.push_back(r);
-            hlinknodes.push_back((int)q);
+            hlinks[(size_t)hslot[q]] = r;
         }
     }
     c->n_link_nodes = (int)hlinknodes.size();
@@ -1171,26 +1178,28 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
     for (int i = 0; i < n_samples; ++i) {
         const HostStencils& H = sts[i]->h;
         const int64_t o = off[i];
+        const bool wr = C.interp != MLBM_INTERP_WLS;
+        if (wr && C.Wr.empty()) C.Wr.assign((size_t)n * 8 * K, 0.0);
+        // every node's rows in parallel (each node writes only its own)
+#pragma omp parallel for schedule(static, 4096)
         for (int64_t p = 0; p < H.n; ++p) {
-            C.perm[o + p] = o + H.perm[p];
+            const size_t g = (size_t)(o + p);
+            C.perm[g] = o + H.perm[p];
             C.inv[o + H.perm[p]] = o + p;
-            for (int j = 0; j < K; ++j) C.idx[(size_t)(o + p) * K + j] = (int32_t)(o + H.idx[(size_t)p * K + j]);
-            C.s_node[o + p] = H.s;
-            node_sample[o + p] = (uint16_t)i;
+            for (int j = 0; j < K; ++j) C.idx[g * K + j] = (int32_t)(o + H.idx[(size_t)p * K + j]);
+            std::copy_n(H.M.begin() + (size_t)p * 6 * K, 6 * K, C.M.begin() + g * 6 * K);
+            if (wr) std::copy_n(H.Wr.begin() + (size_t)p * 8 * K, 8 * K, C.Wr.begin() + g * 8 * K);
+            std::copy_n(H.lag_slot.begin() + (size_t)p * 9, 9, C.lag_slot.begin() + g * 9);
+            std::copy_n(H.q.begin() + (size_t)p * 9, 9, C.q.begin() + g * 9);
+            std::copy_n(H.eqv.begin() + (size_t)p * 3, 3, C.eqv.begin() + g * 3);
+            C.kind[g] = H.kind[p];
+            C.center[g] = H.center[p];
+            C.lag_h[g] = H.lag_h[p];
+            C.link_mask[g] = H.link_mask[p];
+            C.area[g] = H.area[p];
+            C.s_node[g] = H.s;
+            node_sample[g] = (uint16_t)i;
         }
-        std::copy(H.M.begin(), H.M.end(), C.M.begin() + (size_t)o * 6 * K);
-        if (C.interp != MLBM_INTERP_WLS) {
-            if (C.Wr.empty()) C.Wr.assign((size_t)n * 8 * K, 0.0);
-            std::copy(H.Wr.begin(), H.Wr.end(), C.Wr.begin() + (size_t)o * 8 * K);
-        }
-        std::copy(H.kind.begin(), H.kind.end(), C.kind.begin() + o);
-        std::copy(H.center.begin(), H.center.end(), C.center.begin() + o);
-        std::copy(H.lag_h.begin(), H.lag_h.end(), C.lag_h.begin() + o);
-        std::copy(H.lag_slot.begin(), H.lag_slot.end(), C.lag_slot.begin() + (size_t)o * 9);
-        std::copy(H.link_mask.begin(), H.link_mask.end(), C.link_mask.begin() + o);
-        std::copy(H.q.begin(), H.q.end(), C.q.begin() + (size_t)o * 9);
-        std::copy(H.eqv.begin(), H.eqv.end(), C.eqv.begin() + (size_t)o * 3);
-        std::copy(H.area.begin(), H.area.end(), C.area.begin() + o);
         C.info.n_wls += H.info.n_wls;
         C.info.n_lagrange += H.info.n_lagrange;
         C.info.n_eq += H.info.n_eq;
