@@ -410,7 +410,7 @@ def steady_legs(inputs, log):
     sts_tr = W.build(train)
     t_build_tr = time.perf_counter() - t0
     ps_tr = [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, g, 0.0) for _ in train]
-    ru_tr, steps_tr, sec_tr, _ = W.solve(sts_tr, ps_tr, tol=TOL, window=WINDOW, check=CHECK)
+    ru_tr, steps_tr, sec_tr, _ = W.solve(sts_tr, ps_tr, tol=W.TRAIN_TOL, window=WINDOW, check=CHECK)
     del sts_tr
     X = W.features(train)
     T = torch.from_numpy(W.targets(train, ru_tr, ps_tr, 3)).cuda()
@@ -422,7 +422,8 @@ def steady_legs(inputs, log):
     t_train = time.perf_counter() - t0
     out["training"] = {"samples": len(train), "rows": int(X.shape[0]),
                        "nodes_mean": float(np.mean([w.n for w in train])), "seeds_first": int(train[0].meta["seed"]),
-                       "cold_solve_s": sec_tr, "stencil_build_s": t_build_tr, "adam_steps": 8000,
+                       "cold_solve_s": sec_tr, "target_tol": W.TRAIN_TOL, "stencil_build_s": t_build_tr,
+                       "adam_steps": 8000,
                        "train_s": t_train, "minibatch_loss_last": losses[-1]}
     del X, T
     sync()

@@ -468,9 +468,15 @@ mlbm_status mlbm_batch_permeability(mlbm_ctx* ctx, double* k, double* u_superfic
    mlbm_batch_size(ctx) entries (any may be NULL; NULL references give 0 coefficients) */
 mlbm_status mlbm_batch_drag_lift(mlbm_ctx* ctx, const double* ref_length, const double* u_ref, double* fx, double* fy,
                                  double* cd, double* cl);
-/* mlbm_run_to_steady with the criterion per sample; all samples keep stepping
-   until every one has converged or max_steps is reached; steps_taken[i] is the
-   step count at which sample i converged (-1: not converged) */
+/* mlbm_run_to_steady with the criterion per sample; the run goes on until
+   every sample has converged or max_steps is reached; steps_taken[i] is the
+   step count at which sample i converged (-1: not converged).  BGK batches
+   step every sample to the end.  In a tau = 1 batch a converged sample is
+   held at its steady state from then on (its nodes only copy their state,
+   and its criterion is no longer evaluated), so every sample ends in the
+   state a single-sample run of it ends in; the batch's node kinds are the
+   same after the call as before.  The same holds for
+   mlbm_batch_run_to_steady_mean. */
 mlbm_status mlbm_batch_run_to_steady(mlbm_ctx* ctx, double tol, int64_t window, int64_t max_steps,
                                      int64_t* steps_taken);
 mlbm_status mlbm_batch_run_to_steady_ex(mlbm_ctx* ctx, double tol, int64_t window, int64_t check,

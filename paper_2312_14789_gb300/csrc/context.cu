@@ -559,7 +559,12 @@ mlbm_status fields_to_work(mlbm_ctx* c, double* ru_dev_or_null) {
 // Both criteria also check, at every snapshot, that each sample's density is
 // positive and its fields finite on every fluid node (MLBM_E_DIVERGED
 // otherwise).  at[i] receives the step of sample i's steady state, or -1.
-// Steps stop once every sample is steady.
+// Steps stop once every sample is steady.  In a tau = 1 batch a sample that
+// is steady is held at that state while the others go on (its nodes become
+// equilibrium-kind nodes whose record is their state, so each step copies
+// it: ~33 B per node update instead of ~473), and it ends at its own steady
+// step as a single-sample run does; the kind bytes and records are restored
+// when the run ends.
 enum SteadyMode { kFieldNorm = 0, kMeanVelocity = 1 };
 
 mlbm_status run_steady(mlbm_ctx* c, int mode, double tol, int64_t window, int64_t check, int64_t max_steps,
@@ -589,6 +594,28 @@ mlbm_status run_steady(mlbm_ctx* c, int mode, double tol, int64_t window, int64_
             if (ring) cudaFreeAsync(ring, c->stream);
             cudaStreamSynchronize(c->stream);
             return set_error(MLBM_E_OOM, nm + ": " + cudaGetErrorString(e));
+        }
+    }
+    // converged samples of a tau = 1 batch are held (see above)
+    uint8_t* saved_meta = nullptr;
+    float4* saved_eqv = nullptr;
+    bool frozen_any = false;
+    if (c->params.model == MLBM_MODEL_TAU1 && ns > 1 && n > 0) {
+        const size_t np = (size_t)c->n_pad;
+        if (cudaMallocAsync(&saved_meta, np, c->stream) != cudaSuccess ||
+            cudaMallocAsync(&saved_eqv, np * sizeof(float4), c->stream) != cudaSuccess) {
+            (void)cudaGetLastError();  // no room: every sample steps to the end
+            if (saved_meta) cudaFreeAsync(saved_meta, c->stream);
+            saved_meta = nullptr;
+            saved_eqv = nullptr;
+        } else if (cudaMemcpyAsync(saved_meta, c->meta, np, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+                   cudaMemcpyAsync(saved_eqv, c->eqv, np * sizeof(float4), cudaMemcpyDeviceToDevice,
+                                   c->stream) != cudaSuccess) {
+            (void)cudaGetLastError();  // nothing frozen yet: step every sample to the end
+            cudaFreeAsync(saved_meta, c->stream);
+            cudaFreeAsync(saved_eqv, c->stream);
+            saved_meta = nullptr;
+            saved_eqv = nullptr;
         }
     }
     auto slot_u = [&](int64_t k) { return R > 1 ? ring + (size_t)k * 2 * n : c->px; };
@@ -652,15 +679,28 @@ mlbm_status run_steady(mlbm_ctx* c, int mode, double tol, int64_t window, int64_
                 if (steady) {
                     done_at[i] = t;
                     --remaining;
+                    if (saved_meta && remaining > 0) {
+                        const int64_t o = c->seg_off[i];
+                        MLBM_CUDA(launch_freeze_tau1((int)(c->seg_off[i + 1] - o), c->meta + o, c->eqv + o,
+                                                     c->ruv[c->cur] + o, c->stream));
+                        frozen_any = true;
+                    }
                 }
             }
         }
         return remaining == 0 ? MLBM_OK : set_error(MLBM_E_NOT_CONVERGED, nm + ": max_steps reached");
     };
     mlbm_status st = body();
+    if (frozen_any) {
+        const size_t np = (size_t)c->n_pad;
+        cudaMemcpyAsync(c->meta, saved_meta, np, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(c->eqv, saved_eqv, np * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (saved_meta) cudaFreeAsync(saved_meta, c->stream);
+    if (saved_eqv) cudaFreeAsync(saved_eqv, c->stream);
     if (ring) cudaFreeAsync(ring, c->stream);
     if (means) cudaFreeAsync(means, c->stream);
-    if (ring || means) cudaStreamSynchronize(c->stream);
+    if (ring || means || saved_meta) cudaStreamSynchronize(c->stream);
     if (at)
         for (int i = 0; i < ns; ++i) at[i] = done_at[i];
     return st;

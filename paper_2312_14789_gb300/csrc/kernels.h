@@ -37,6 +37,10 @@ cudaError_t launch_get_bgk(int n, const int* perm, const float4* f8, const float
 cudaError_t launch_set_bgk_equilibrium(int n, const int* perm, const double* ru, float4* f8, float* f0,
                                        cudaStream_t st);
 cudaError_t launch_set_tau1(int n, const int* perm, const double* ru, float4* s, cudaStream_t st);
+// tau = 1: holds the m nodes' states fixed in later steps by making them
+// equilibrium-kind nodes whose record is their current state (run to steady
+// state of a batch: samples that have converged)
+cudaError_t launch_freeze_tau1(int m, uint8_t* meta, float4* eqv, const float4* state, cudaStream_t st);
 cudaError_t launch_get_tau1(int n, const int* perm, const float4* s, double* ru, cudaStream_t st);
 cudaError_t launch_macroscopics(int model, int n, const int* perm, const float4* f8, const float* f0,
                                 const float4* ruv, float ax, float ay, const uint16_t* node_sample,

@@ -31,6 +31,10 @@ from . import mlbm
 
 TOL, WINDOW = 1e-7, 1000   # steady when |u(t) - u(t - W)| / (W |u(t)|) < TOL
 CHECK = 100                # the criterion is evaluated every CHECK steps
+# training samples are solved ten times below the criterion the warm start is
+# judged by, so that the targets stand for the steady state rather than the
+# first state that passes the criterion
+TRAIN_TOL = 1e-8
 
 
 def length_scale(w) -> float:

@@ -72,6 +72,41 @@ def test_batch_run_to_steady_reports_each_sample():
     assert taken[0] < taken[1]  # the narrower channel relaxes first
 
 
+@pytest.mark.parametrize("criterion", ["field_norm", "mean_velocity"])
+@pytest.mark.parametrize("variant", [25, 5])
+def test_batch_run_to_steady_holds_converged_samples(criterion, variant):
+    """A tau = 1 batch holds each converged sample at its steady state: every
+    sample ends bit for bit where a single-sample run of it ends, at the same
+    step, and the batch's node kinds are restored afterwards (its next steps
+    equal those of a fresh batch loaded with the same fields)."""
+    ws, ss, ps = _samples()
+    sts = [mlbm.build_stencils_for(w, K=16, s=s, bb_mode=1) for w, s in zip(ws, ss)]
+    batch = mlbm.batch_init(sts, ps)
+    mlbm.set_kernel_variant(batch, variant)
+    if criterion == "field_norm":
+        run_b = lambda c: mlbm.batch_run_to_steady(c, 1e-6, 200, 40000, check=100)
+        run_1 = lambda c: mlbm.run_to_steady(c, 1e-6, 200, 40000, check=100)
+    else:
+        run_b = lambda c: mlbm.batch_run_to_steady_mean(c, 5e-2, 1000, 100, [1e-4] * 3, max_steps=40000)
+        run_1 = lambda c: mlbm.run_to_steady_mean(c, 5e-2, 1000, 100, 1e-4, max_steps=40000)
+    taken = run_b(batch)
+    assert len(set(int(t) for t in taken)) > 1   # the samples converge at different steps
+    fb = mlbm.get_fields(batch)
+    for i, (st, p) in enumerate(zip(sts, ps)):
+        ctx = mlbm.init(st, p)
+        mlbm.set_kernel_variant(ctx, variant)
+        t1 = run_1(ctx)
+        first, count = mlbm.batch_range(batch, i)
+        assert int(taken[i]) == int(t1)
+        assert np.array_equal(fb[first:first + count], mlbm.get_fields(ctx)), i
+    fresh = mlbm.batch_init(sts, ps)
+    mlbm.set_kernel_variant(fresh, variant)
+    mlbm.set_fields(fresh, fb)
+    mlbm.step(batch, 37)
+    mlbm.step(fresh, 37)
+    assert np.array_equal(mlbm.get_fields(batch), mlbm.get_fields(fresh))
+
+
 def test_graph_replay_matches_direct_launches():
     w = I.porous(seed=34, n_target=8000)
     st = mlbm.build_stencils_for(w, K=16, s=0.5, bb_mode=1)

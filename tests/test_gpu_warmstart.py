@@ -30,7 +30,7 @@ def test_warm_start_reaches_steady_state_sooner():
 
     sts = W.build(ws_train)
     ps = par(ws_train)
-    ru, _, _, _ = W.solve(sts, ps)
+    ru, _, _, _ = W.solve(sts, ps, tol=W.TRAIN_TOL)
     del sts
     X = W.features(ws_train)
     T = torch.from_numpy(W.targets(ws_train, ru, ps, 3)).cuda()
