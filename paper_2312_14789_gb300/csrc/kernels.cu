@@ -398,26 +398,6 @@ cudaError_t launch_set_tau1(int n, const int* perm, const double* ru, float4* s,
     dev::set_tau1_from_f64<<<blocks_for(n, 256), 256, 0, st>>>(n, perm, ru, s);
     return cudaGetLastError();
 }
-namespace dev {
-// tau = 1: a node of the equilibrium kind copies its stored record (rho - 1,
-// u, v, 0) to the output every step; making every node of a sample such a
-// node, with its current state as the record, holds the sample's state fixed
-__global__ void freeze_tau1(int m, uint8_t* __restrict__ meta, float4* __restrict__ eqv,
-                            const float4* __restrict__ state) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m) return;
-    const uint8_t t = meta[p];
-    if ((t & 3) != 2) {
-        eqv[p] = state[p];
-        meta[p] = (uint8_t)((t & ~3u) | 2u);
-    }
-}
-}  // namespace dev
-cudaError_t launch_freeze_tau1(int m, uint8_t* meta, float4* eqv, const float4* state, cudaStream_t st) {
-    if (m == 0) return cudaSuccess;
-    dev::freeze_tau1<<<blocks_for(m, 256), 256, 0, st>>>(m, meta, eqv, state);
-    return cudaGetLastError();
-}
 cudaError_t launch_get_tau1(int n, const int* perm, const float4* s, double* ru, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     dev::get_tau1_to_f64<<<blocks_for(n, 256), 256, 0, st>>>(n, perm, s, ru);
