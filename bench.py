@@ -27,6 +27,13 @@ velocity over 2e4 steps per unit time below 1e-2) on the cold batch.
 40 spacings, ~260k nodes, BGK, simple bounce-back; the six runs Re in
 {100, 200} x s in {1/2, 1/4, 1/8} in one batched context).
 
+`--workload lattice_compare`: the paper's comparison with lattice LBM (Sec.
+3.1), the vortex street at Re = 100: the lattice (D = 80 spacings) against
+the meshless step on the scattered, hybrid and coarsened hybrid node sets
+and with the paper's RBF-FD interpolant (D = 40 node spacings, s = 1/2): time
+per step of each and, over --vortex-steps from rest, Strouhal number and
+drag; `value` is the scattered least-squares rate.
+
 `--workload porous_box`: one porous sample of Sec. 3.2 at full size (seed 3,
 ~960k nodes, porosity 0.7, K = 16, tau = 1, interpolated bounce-back, s = 1/2,
 g = 1e-5 along x); ~450 MB of stencil rows per step, larger than L2, so
@@ -82,16 +89,17 @@ def tau_of(re, s):
     return 3.0 * U0 * (D / s) / re + 0.5
 
 
-def algorithmic_bytes(info, K, model="bgk"):
+def algorithmic_bytes(info, K, model="bgk", rows=6):
     """Bytes one fused step must move at minimum, per node kind.
     BGK: least-squares node 4*(9+9) populations + 4*6K matrix + 4K indices +
-    1 meta; Lagrange node 4*(9+9) + 4*12 indices + 4 (s/h) + 1; equilibrium
+    1 meta (RBF-FD stencils: rows = 8 weight rows instead of the 6 matrix
+    rows); Lagrange node 4*(9+9) + 4*12 indices + 4 (s/h) + 1; equilibrium
     node 16 + 36 + 1.  tau = 1: the state is (rho, u_x, u_y), 3 floats read
     and 3 written, so 4*(3+3) replaces 4*(9+9) and an equilibrium node costs
     12 + 12 + 1 (the 16-byte padding of the stored state is not the method's
     work and is not counted)."""
     state = 4 * 6 if model == "tau1" else 4 * 18
-    wls = state + 4 * 6 * K + 4 * K + 1
+    wls = state + 4 * rows * K + 4 * K + 1
     lag = state + 4 * 12 + 4 + 1
     eq = 12 + 12 + 1 if model == "tau1" else 16 + 36 + 1
     return info["n_wls"] * wls + info["n_lagrange"] * lag + info["n_eq"] * eq
@@ -203,7 +211,7 @@ def make_inputs(args, rank, world):
     """Node sets of this rank (spawned worker processes; called before CUDA
     is touched)."""
     from paper_2312_14789_gb300 import inputs as I
-    if args.workload == "karman_sweep":
+    if args.workload in ("karman_sweep", "lattice_compare"):
         return {"karman": I.karman(seed=2)}
     if args.workload == "porous_box":
         return {"box": I.porous(seed=BOX_SEED + rank)}
@@ -239,6 +247,10 @@ def build_batch(args, inputs):
 
 
 def workload_config(args, inputs, infos, n, world):
+    if args.workload == "lattice_compare":
+        return {"workload": "karman_lattice_vs_meshless", "Re": LC_RE, "U0": U0, "D_node_spacings": D, "s": LC_S,
+                "nodes": inputs["karman"].n, "seed": 2, "node_updates_per_step": n,
+                "timed_here": "the meshless step on the scattered set (the oracle's BGK step)"}
     if args.workload == "karman_sweep":
         w = inputs["karman"]
         return {"workload": "karman_vortex_street_sweep",
@@ -273,7 +285,7 @@ def oracle_sample_rate(args, inputs, n_sample, seed, min_seconds=0.0, max_reps=1
     Returns (Mnode-updates/s, threads, description, seconds per step)."""
     import oracle as O
     rng = np.random.default_rng(seed)
-    if args.workload == "karman_sweep":
+    if args.workload in ("karman_sweep", "lattice_compare"):
         w, s, model = inputs["karman"], 0.5, "bgk"
         what = f"the {w.n}-node vortex-street node set (Re = 100, s = 1/2)"
     elif args.workload == "porous_box":
@@ -308,6 +320,8 @@ def run_reference(args, rank, world):
     inputs = make_inputs(argparse.Namespace(**{**vars(args), "steady": False}), 0, 1)
     if args.workload == "karman_sweep":
         n = inputs["karman"].n * len(CASES)
+    elif args.workload == "lattice_compare":
+        n = inputs["karman"].n
     elif args.workload == "porous_box":
         n = inputs["box"].n
     else:
@@ -628,13 +642,185 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(out))
 
 
+# ------------------------------------------- lattice LBM vs meshless (Sec. 3.1)
+LC_RE, LC_S, LC_EVERY = 100, 0.5, 50
+
+
+def strouhal_of(cl, every, d_lb, u0):
+    """St = f D / U0 from the mean spacing of the upward zero crossings of
+    C_L - mean(C_L), interpolated linearly between samples; None with fewer
+    than three crossings."""
+    c = np.asarray(cl, np.float64) - np.mean(cl)
+    i = np.nonzero((c[:-1] < 0) & (c[1:] >= 0))[0]
+    if len(i) < 3:
+        return None
+    tz = (i + (-c[i]) / (c[i + 1] - c[i])) * every
+    return float(d_lb / (np.mean(np.diff(tz)) * u0))
+
+
+def lattice_compare_methods():
+    """(name, node set, interpolant, K, weight rows) of the meshless runs."""
+    from paper_2312_14789_gb300 import inputs as I
+    from paper_2312_14789_gb300 import mlbm
+    return [("meshless_scattered", I.karman(seed=2), mlbm.INTERP_WLS, 16, 6),
+            ("meshless_hybrid", I.karman(seed=2, lattice_beyond_d=1.0), mlbm.INTERP_WLS, 16, 6),
+            ("meshless_hybrid_coarse", I.karman(seed=2, lattice_beyond_d=1.0, coarse_beyond_d=2.0),
+             mlbm.INTERP_WLS, 16, 6),
+            ("meshless_scattered_rbf_points", I.karman(seed=2), mlbm.INTERP_RBF_POINTS, 64, 8)]
+
+
+def run_lattice_compare(args, rank, local_rank):
+    """The paper's comparison of lattice LBM and meshless LBM (Sec. 3.1) on
+    one GPU.  The vortex street at Re = 100: the regular lattice with D = 80
+    spacings (equilibrium sides, half-way bounce-back, the meshless step's
+    FP32 collision) against the meshless step on node sets with D = 40 node
+    spacings and s = 1/2, which take the same time step.  The node sets:
+    scattered least squares; hybrid (Lagrange bulk beyond 1 D); coarsened
+    hybrid (spacing 2 beyond 2 D); and the paper's RBF-FD interpolant with a
+    stencil per Lagrangian point (the 25 nearest nodes).  Per method: time per
+    step (CUDA events, `--steps` steps back to back after `--warmup`, variant
+    from the autotuner), node updates per second, and, with --vortex-steps >
+    0, the Strouhal number and mean drag over the second half of that many
+    steps from rest (momentum exchange; for the meshless sets also the
+    stress integrated along the cylinder's wall nodes).  `value` is the
+    scattered least-squares rate.  Rank 0 only."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2312_14789_gb300 import inputs as I
+    from paper_2312_14789_gb300 import mlbm
+    torch.cuda.set_device(local_rank)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    u0, d = U0, D
+    d_lb = d / LC_S
+    tau = 3.0 * u0 * d_lb / LC_RE + 0.5
+    p = mlbm.Params(mlbm.MODEL_BGK, tau, 0.0, 0.0, 0.0)
+    n_rec = args.vortex_steps // LC_EVERY
+    half = n_rec // 2
+    comp = {}
+    clocks = Clocks(local_rank)
+
+    # lattice LBM
+    cell, eqv = I.karman_lattice(d_lb, u0)
+    lat = mlbm.Lattice(cell, p, periodic=(False, False), eq_values=eqv)
+    lat.time_steps(args.warmup)
+    us_lat = lat.time_steps(args.steps) * 1e3 / args.steps
+    n_lat = int((cell != 1).sum())
+    comp["lattice"] = {"cells": int(cell.size), "fluid_and_boundary_cells": n_lat, "us_per_step": us_lat,
+                       "mnups": n_lat / us_lat, "algorithmic_bytes_per_step": int(cell.size) * 73}
+    if n_rec:
+        lat = mlbm.Lattice(cell, p, periodic=(False, False), eq_values=eqv)
+        cd, cl = np.empty(n_rec), np.empty(n_rec)
+        for i in range(n_rec):
+            lat.step(LC_EVERY)
+            fx, fy = lat.force()
+            cd[i], cl[i] = 2 * fx / (u0 ** 2 * d_lb), 2 * fy / (u0 ** 2 * d_lb)
+        comp["lattice"].update(strouhal=strouhal_of(cl[half:], LC_EVERY, d_lb, u0),
+                               cd_mean=float(np.mean(cd[half:])), cl_amplitude=float(np.ptp(cl[half:]) / 2))
+    del lat
+    log(f"lattice: {us_lat:.2f} us/step")
+    return lattice_compare_meshless(args, comp, p, tau, d_lb, n_rec, half, clocks, log)
+
+
+def lattice_compare_meshless(args, comp, p, tau, d_lb, n_rec, half, clocks, log):
+    """The meshless half of run_lattice_compare, then its JSON line."""
+    import torch
+    from paper_2312_14789_gb300 import inputs as I
+    from paper_2312_14789_gb300 import mlbm
+    u0, d = U0, D
+    keep = {}
+    for name, w, interp, K, rows in lattice_compare_methods():
+        st = mlbm.build_stencils_for(w, K=K, s=LC_S, bb_mode=mlbm.BB_SIMPLE, interp=interp, n_l=25)
+        info = mlbm.stencils_info(st)
+        ctx = mlbm.init(st, p)
+        variant, _ = mlbm.autotune(ctx, 5)
+        stream = torch.cuda.Stream()
+        mlbm.set_stream(ctx, stream.cuda_stream)
+        mlbm.prepare_graphs(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            mlbm.step(ctx, args.warmup)
+            e0.record(stream)
+            mlbm.step(ctx, args.steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / args.steps
+        r = {"nodes": int(w.n), "n_lagrange": int(info["n_lagrange"]), "K": K, "variant": int(variant),
+             "us_per_step": us, "mnups": w.n / us, "time_per_step_over_lattice": us / comp["lattice"]["us_per_step"],
+             "algorithmic_bytes_per_step": int(algorithmic_bytes(info, K, "bgk", rows))}
+        if n_rec:
+            ctx = mlbm.init(st, p)
+            mlbm.set_kernel_variant(ctx, variant)
+            geo = I.wall_geometry(w)
+            cd, cl, cds, cls = (np.empty(n_rec) for _ in range(4))
+            for i in range(n_rec):
+                mlbm.step(ctx, LC_EVERY)
+                _, _, cd[i], cl[i] = mlbm.drag_lift(ctx, d, u0)
+                fx, fy = mlbm.wall_stress_force(ctx, *geo)
+                cds[i], cls[i] = 2 * fx / (u0 ** 2 * d_lb), 2 * fy / (u0 ** 2 * d_lb)
+            r.update(strouhal=strouhal_of(cl[half:], LC_EVERY, d_lb, u0), cd_mean=float(np.mean(cd[half:])),
+                     cl_amplitude=float(np.ptp(cl[half:]) / 2), cd_mean_stress=float(np.mean(cds[half:])))
+        comp[name] = r
+        log(f"{name}: {us:.2f} us/step (variant {variant})")
+        if name == "meshless_scattered":
+            keep = {"w": w, "st": st, "info": info, "variant": variant, "us": us}
+        del ctx, st
+    clk = clocks.stop()
+    # end to end on the scattered set: populations up from pinned memory,
+    # the timed steps, populations and the drag back
+    w, info = keep["w"], keep["info"]
+    ctx = mlbm.init(keep["st"], p)
+    mlbm.set_kernel_variant(ctx, keep["variant"])
+    f_in = torch.empty((w.n, 9), dtype=torch.float64, pin_memory=True).numpy()
+    f_in[:] = mlbm.get_populations(ctx)
+    f_out = torch.empty((w.n, 9), dtype=torch.float64, pin_memory=True).numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mlbm.set_populations(ctx, f_in)
+    mlbm.step(ctx, args.steps)
+    assert mlbm.lib().mlbm_get_populations(ctx.handle, f_out.ctypes.data) == 0
+    mlbm.drag_lift(ctx, d, u0)
+    e2e_s = time.perf_counter() - t0
+    del ctx
+    pk, pk_kind = peaks()
+    keep_bytes = comp["meshless_scattered"]["algorithmic_bytes_per_step"]
+    achieved = keep_bytes / (keep["us"] * 1e-6) / 1e9
+    cpu_val, cpu_threads, cpu_desc, _ = oracle_sample_rate(argparse.Namespace(workload="karman_sweep"),
+                                                           {"karman": w}, ORACLE_SAMPLE, 1, min_seconds=10.0,
+                                                           max_reps=20000)
+    print(json.dumps({
+        "metric": METRIC, "value": w.n / keep["us"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": keep["us"] / 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "karman_lattice_vs_meshless", "Re": LC_RE, "U0": u0, "D_node_spacings": d, "s": LC_S,
+                   "D_lattice_spacings": d_lb, "tau": tau, "vortex_steps": args.vortex_steps,
+                   "sample_every": LC_EVERY, "node_areas": "fluid-Voronoi", "bounce_back": "simple (meshless), "
+                   "half-way (lattice)", "seed": 2,
+                   "l2": "working sets of 33-134 MB, largely L2-resident: steps timed back to back, no flush; "
+                         "these are latency numbers, not HBM fractions"},
+        "comparison": comp,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "note": f"the scattered least-squares step: {keep_bytes} algorithmic bytes per launch "
+                             f"(521 B per least-squares node update); the node set is L2-resident, so part of "
+                             f"these bytes come from L2; peak {pk_kind} burst copy"},
+        "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cpu_threads, "kind": "oracle", "sample": cpu_desc},
+        "e2e": {"value": w.n * args.steps / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": w.n * 72 / args.steps,
+                "d2h_bytes_per_step": (w.n * 72 + 32) / args.steps,
+                "note": f"set_populations from pinned host memory + {args.steps} steps + get_populations + drag, "
+                        "wall clock, scattered set"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="porous_batch", choices=["porous_batch", "karman_sweep", "porous_box"])
+    ap.add_argument("--workload", default="porous_batch", choices=["porous_batch", "karman_sweep", "porous_box", "lattice_compare"])
     ap.add_argument("--samples", type=int, default=64, help="porous samples per batch (64: the configuration)")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"])
     ap.add_argument("--variant", type=int, default=-1,
@@ -645,6 +831,8 @@ def main():
     ap.add_argument("--steady-samples", type=int, default=8)
     ap.add_argument("--train-samples", type=int, default=32)
     ap.add_argument("--train-nodes", type=int, default=100_000)
+    ap.add_argument("--vortex-steps", type=int, default=200_000,
+                    help="lattice_compare: steps from rest for the Strouhal number and drag (0: timing only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -653,6 +841,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "lattice_compare":
+        run_lattice_compare(args, rank, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -500,6 +500,29 @@ def cylinder_array(side: float = 40.0, radius: float = 8.0, h: float = 1.0, seed
                     {"seed": seed, "solid_fraction": float(np.pi * radius ** 2 / side ** 2), "L": side})
 
 
+def karman_lattice(d_lb: float, u0: float = 0.05, length_d: float = 22.0, height_d: float = 4.1,
+                   center_d: tuple = (2.0, 2.0)):
+    """The vortex-street channel of `karman` on a regular lattice (the lattice
+    LBM comparison of Sec. 3.1): D = d_lb lattice spacings, cells (ny, nx)
+    with class 0 fluid, 1 solid (cell centre inside the cylinder), 2
+    equilibrium (the four sides: parabolic inflow and outflow with maximum u0,
+    rest on the top and bottom, unit density).  Returns (cell, eq_values
+    [ny][nx][3] = rho, ux, uy)."""
+    nx, ny = int(round(length_d * d_lb)), int(round(height_d * d_lb))
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    cx, cy, r = center_d[0] * d_lb, center_d[1] * d_lb, 0.5 * d_lb
+    cell = np.zeros((ny, nx), np.uint8)
+    cell[(x - cx) ** 2 + (y - cy) ** 2 < r * r] = 1
+    top_bottom = (y == 0) | (y == ny - 1)
+    left_right = (x == 0) | (x == nx - 1)
+    cell[top_bottom | left_right] = 2
+    eqv = np.zeros((ny, nx, 3))
+    eqv[..., 0] = 1.0
+    h = ny - 1.0
+    eqv[..., 1] = np.where(left_right & ~top_bottom, 4.0 * u0 * y * (h - y) / (h * h), 0.0)
+    return cell, eqv
+
+
 def wall_geometry(w: Workload, tol: float = 1e-6):
     """Wall nodes on the solid disks and on the straight solid sides of a node
     set, with the unit normal pointing out of the solid into the fluid and the

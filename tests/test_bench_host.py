@@ -98,3 +98,27 @@ def test_ranks_share_the_host_cores(monkeypatch):
     monkeypatch.setenv("LOCAL_WORLD_SIZE", "1")
     bench.share_host_cores(1)
     assert "OMP_NUM_THREADS" not in bench.os.environ
+
+
+def test_strouhal_of_a_sampled_sine():
+    """St = D / (period U0): a C_L series with a period of 1234.5 steps,
+    sampled every 50 steps, gives its frequency back from the zero crossings."""
+    import numpy as np
+    every, d_lb, u0, period = 50, 80.0, 0.05, 1234.5
+    t = np.arange(0, 200_000, every, dtype=np.float64)
+    cl = 0.02 + 0.3 * np.sin(2 * np.pi * t / period + 0.4)
+    st = bench.strouhal_of(cl, every, d_lb, u0)
+    assert abs(st / (d_lb / (period * u0)) - 1) < 1e-4
+    assert bench.strouhal_of(np.ones(10), every, d_lb, u0) is None
+
+
+def test_karman_lattice_cells():
+    import numpy as np
+    cell, eqv = I.karman_lattice(80.0)
+    assert cell.shape == (328, 1760)
+    assert abs((cell == 1).sum() / (np.pi * 40.0 ** 2) - 1) < 0.01     # the cylinder's area
+    assert np.all(cell[0] == 2) and np.all(cell[-1] == 2) and np.all(cell[:, 0] == 2) and np.all(cell[:, -1] == 2)
+    # parabolic inflow with maximum U0 = 0.05 across the channel, rest on top and bottom
+    h = cell.shape[0] - 1.0
+    assert abs(eqv[int(h // 2), 0, 1] - 0.05 * 4 * (h // 2) * (h - h // 2) / h ** 2) < 1e-15
+    assert eqv[0, 0, 1] == 0.0 and np.all(eqv[..., 0] == 1.0)
