@@ -751,15 +751,17 @@ def lattice_compare_meshless(args, comp, p, tau, d_lb, n_rec, half, clocks, log)
         if n_rec:
             ctx = mlbm.init(st, p)
             mlbm.set_kernel_variant(ctx, variant)
-            geo = I.wall_geometry(w)
-            cd, cl, cds, cls = (np.empty(n_rec) for _ in range(4))
+            # the stress-integrated force needs the least-squares fit
+            geo = I.wall_geometry(w) if interp == mlbm.INTERP_WLS else None
+            cd, cl, cds = np.empty(n_rec), np.empty(n_rec), np.empty(n_rec)
             for i in range(n_rec):
                 mlbm.step(ctx, LC_EVERY)
                 _, _, cd[i], cl[i] = mlbm.drag_lift(ctx, d, u0)
-                fx, fy = mlbm.wall_stress_force(ctx, *geo)
-                cds[i], cls[i] = 2 * fx / (u0 ** 2 * d_lb), 2 * fy / (u0 ** 2 * d_lb)
+                if geo is not None:
+                    cds[i] = 2 * mlbm.wall_stress_force(ctx, *geo)[0] / (u0 ** 2 * d_lb)
             r.update(strouhal=strouhal_of(cl[half:], LC_EVERY, d_lb, u0), cd_mean=float(np.mean(cd[half:])),
-                     cl_amplitude=float(np.ptp(cl[half:]) / 2), cd_mean_stress=float(np.mean(cds[half:])))
+                     cl_amplitude=float(np.ptp(cl[half:]) / 2),
+                     cd_mean_stress=float(np.mean(cds[half:])) if geo is not None else None)
         comp[name] = r
         log(f"{name}: {us:.2f} us/step (variant {variant})")
         if name == "meshless_scattered":
