@@ -38,7 +38,9 @@ drag; `value` is the scattered least-squares rate.
 ~960k nodes, porosity 0.7, K = 16, tau = 1, interpolated bounce-back, s = 1/2,
 g = 1e-5 along x); ~450 MB of stencil rows per step, larger than L2, so
 steps are timed back to back.  Under torchrun every rank steps its own box
-(seed 3 + rank).
+(seed 3 + rank).  After the timed steps (N = 1 only, unless --no-steady) the
+box runs from rest to steady state at four (s, g): one Darcy and three
+inertial runs.
 
 Arms:
   default            the CUDA path through the C ABI (device-resident state)
@@ -374,6 +376,41 @@ def job_rate(total_node_updates, ms):
     return total_node_updates / (ms / 1e3) / 1e6
 
 
+# the porous box to steady state: (s, g) of a Darcy and three inertial runs
+BOX_STEADY = [(1.0, 1e-6), (0.5, 8e-5), (0.25, 2e-5), (0.125, 5e-6)]
+
+
+def box_steady_legs(w, log):
+    """The single porous box from rest to steady state (the criterion of the
+    time-to-steady legs) at each (s, g) of BOX_STEADY: steps, seconds
+    (context creation, run and observables), permeability in units of s^2
+    and of the node spacing, tortuosity and the grain Reynolds numbers
+    Re_d = U d / nu with d the mean disk diameter in units of s and U the
+    superficial velocity (re_d) or the mean pore velocity (re_d_intrinsic)."""
+    import torch
+    from paper_2312_14789_gb300 import mlbm
+    nu = (1.0 - 0.5) / 3.0
+    d_mean = 2.0 * float(np.mean(w.disks[:, 2]))
+    out = {"criterion": f"|u(t) - u(t-{WINDOW})| / ({WINDOW} |u(t)|) < {TOL:g}, checked every {CHECK} steps",
+           "nodes": w.n, "node_areas": "uniform", "runs": []}
+    for s, g in BOX_STEADY:
+        st = mlbm.build_stencils_for(w, K=16, s=s, bb_mode=mlbm.BB_INTERPOLATED)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = mlbm.init(st, mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, g, 0.0))
+        steps = mlbm.run_to_steady(ctx, TOL, WINDOW, 400_000, check=CHECK)
+        pm = mlbm.permeability(ctx)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        out["runs"].append({"s": s, "g": g, "steps": int(steps), "seconds": sec, "mnups": w.n * steps / sec / 1e6,
+                            "k": pm["k"], "k_node_spacing_units": pm["k"] * s * s,
+                            "tortuosity": pm["tortuosity"], "re_d": pm["u_superficial"] * (d_mean / s) / nu,
+                            "re_d_intrinsic": pm["u_intrinsic"] * (d_mean / s) / nu})
+        log(f"box s = {s}: {steps} steps, {sec:.2f} s")
+        del ctx, st
+    return out
+
+
 def steady_legs(inputs, log):
     """Time to steady state on held-out porous samples: cold single-instance,
     cold batched, learned warm start (batched and single), and the paper's
@@ -603,6 +640,8 @@ def run_ours(args, rank, world, local_rank):
     steady = None
     if rank == 0 and world == 1 and args.steady and args.workload == "porous_batch":
         steady = steady_legs(inputs, log)
+    elif rank == 0 and world == 1 and args.steady and args.workload == "porous_box":
+        steady = box_steady_legs(inputs["box"], log)
     clk = clocks.stop() if clocks else None
     if rank != 0:
         return
