@@ -251,6 +251,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
             hlinknodes.push_back((int)q);
         }
     hlinks.resize(hlinknodes.size());
+    const bool parts = !H.part_off.empty();
 #pragma omp parallel for schedule(static, 4096)
     for (int64_t q = 0; q < n; ++q) {
         const uint8_t kind = H.kind[q];
@@ -274,11 +275,24 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
                 std::sort(order, order + K, [&](int a, int b) {
                     return H.slot_key[(size_t)q * K + a] < H.slot_key[(size_t)q * K + b];
                 });
+            // the node's matrix (and RBF-FD weight) rows: its own, or its sample's
+            const double* Mq;
+            const double* Wq = nullptr;
+            if (parts) {
+                const size_t i =
+                    (size_t)(std::upper_bound(H.part_off.begin(), H.part_off.end(), q) - H.part_off.begin()) - 1;
+                const size_t l = (size_t)(q - H.part_off[i]);
+                Mq = H.part_M[i] + l * 6 * K;
+                if (rbf) Wq = H.part_Wr[i] + l * 8 * K;
+            } else {
+                Mq = H.M.data() + (size_t)q * 6 * K;
+                if (rbf) Wq = H.Wr.data() + (size_t)q * 8 * K;
+            }
             for (int jj = 0; jj < K; ++jj) {
                 const int j = order[jj];
                 hidx[(((size_t)(jj / 4)) * np + q) * 4 + (jj % 4)] = H.idx[(size_t)q * K + j];
                 double m[6];
-                for (int a = 0; a < 6; ++a) m[a] = H.M[((size_t)q * 6 + a) * K + j];
+                for (int a = 0; a < 6; ++a) m[a] = Mq[(size_t)a * K + j];
                 // D2Q9 departure basis (see device_common.cuh), formed in FP64
                 const double t[6] = {m[0] + m[3], m[0] + m[5], m[0] + m[3] + m[4] + m[5], m[0] + m[3] - m[4] + m[5],
                                      m[1], m[2]};
@@ -287,7 +301,7 @@ mlbm_status do_init(mlbm_ctx* c, const mlbm_stencils* st, const mlbm_params* p, 
                 if (rbf)
                     for (int k = 0; k < 8; ++k)
                         hW[(((size_t)(k * Kq + jj / 4)) * np + q) * 4 + (jj % 4)] =
-                            (float)H.Wr[((size_t)q * 8 + k) * K + j];
+                            (float)Wq[(size_t)k * K + j];
             }
         } else if (kind == kKindLagrange) {
             for (int b = 0; b < 9; ++b) {
@@ -1210,7 +1224,7 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
     }
     C.n = n;
     C.box_area = 0;
-    C.perm.resize(n); C.inv.resize(n); C.idx.resize((size_t)n * K); C.M.resize((size_t)n * 6 * K);
+    C.perm.resize(n); C.inv.resize(n); C.idx.resize((size_t)n * K);
     C.kind.resize(n); C.center.resize(n); C.lag_h.resize(n); C.lag_slot.resize((size_t)n * 9);
     C.link_mask.resize(n); C.q.resize((size_t)n * 9); C.eqv.resize((size_t)n * 3); C.area.resize(n);
     C.s_node.resize(n);
@@ -1219,7 +1233,9 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
         const HostStencils& H = sts[i]->h;
         const int64_t o = off[i];
         const bool wr = C.interp != MLBM_INTERP_WLS;
-        if (wr && C.Wr.empty()) C.Wr.assign((size_t)n * 8 * K, 0.0);
+        // the matrix and weight rows stay in the sample's stencils
+        C.part_M.push_back(H.M.data());
+        C.part_Wr.push_back(wr ? H.Wr.data() : nullptr);
         // every node's rows in parallel (each node writes only its own)
 #pragma omp parallel for schedule(static, 4096)
         for (int64_t p = 0; p < H.n; ++p) {
@@ -1227,8 +1243,6 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
             C.perm[g] = o + H.perm[p];
             C.inv[o + H.perm[p]] = o + p;
             for (int j = 0; j < K; ++j) C.idx[g * K + j] = (int32_t)(o + H.idx[(size_t)p * K + j]);
-            std::copy_n(H.M.begin() + (size_t)p * 6 * K, 6 * K, C.M.begin() + g * 6 * K);
-            if (wr) std::copy_n(H.Wr.begin() + (size_t)p * 8 * K, 8 * K, C.Wr.begin() + g * 8 * K);
             std::copy_n(H.lag_slot.begin() + (size_t)p * 9, 9, C.lag_slot.begin() + g * 9);
             std::copy_n(H.q.begin() + (size_t)p * 9, 9, C.q.begin() + g * 9);
             std::copy_n(H.eqv.begin() + (size_t)p * 3, 3, C.eqv.begin() + g * 3);
@@ -1246,6 +1260,7 @@ mlbm_status mlbm_batch_init(mlbm_ctx** out, const mlbm_stencils* const* sts, con
         C.info.n_link_nodes += H.info.n_link_nodes;
         C.info.n_links += H.info.n_links;
     }
+    C.part_off = off;
     C.info.n = n;
     C.info.K = K;
     int ndev = 0;

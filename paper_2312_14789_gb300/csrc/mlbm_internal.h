@@ -53,6 +53,11 @@ struct HostStencils {
     // that a partition sums its stencil in the same order; idx when empty)
     int64_t n_halo = 0;
     std::vector<int64_t> slot_key;  // [n][K]
+    // a batch's concatenation keeps no M or Wr of its own: the rows of node q
+    // of sample i (part_off[i] <= q < part_off[i + 1]) are read from that
+    // sample's stencils, part_M[i] (and part_Wr[i]) at q - part_off[i]
+    std::vector<const double*> part_M, part_Wr;
+    std::vector<int64_t> part_off;
 };
 
 // Partition of a node set into contiguous ranges of device positions (Hilbert

@@ -44,6 +44,27 @@ def test_batch_samples_evolve_as_alone(variant):
         assert pb["k"][i] == pm["k"] and pb["tortuosity"][i] == pm["tortuosity"]
 
 
+@pytest.mark.parametrize("interp", ["rbf", "rbf_points"])
+def test_rbf_batch_samples_evolve_as_alone(interp):
+    """RBF-FD stencils in a batch (the weight rows are read from each
+    sample's own stencils when the batch is built): every sample evolves
+    exactly as alone."""
+    ws, ss, ps = _samples()
+    if interp == "rbf":
+        sts = [mlbm.build_stencils_for(w, K=16, s=s, bb_mode=1, interp=mlbm.INTERP_RBF) for w, s in zip(ws, ss)]
+    else:
+        sts = [mlbm.build_stencils_for(w, K=64, s=s, bb_mode=1, interp=mlbm.INTERP_RBF_POINTS, n_l=25)
+               for w, s in zip(ws, ss)]
+    batch = mlbm.batch_init(sts, ps)
+    mlbm.step(batch, 25)
+    fb = mlbm.get_fields(batch)
+    for i, (st, p) in enumerate(zip(sts, ps)):
+        ctx = mlbm.init(st, p)
+        mlbm.step(ctx, 25)
+        first, count = mlbm.batch_range(batch, i)
+        assert np.array_equal(fb[first:first + count], mlbm.get_fields(ctx)), i
+
+
 def test_batch_bgk_with_per_sample_tau():
     w1 = I.poiseuille_channel(20, 16, 0.2, seed=3)
     w2 = I.poiseuille_channel(24, 20, 0.2, seed=4)
