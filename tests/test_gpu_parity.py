@@ -586,3 +586,43 @@ def test_karman_sweep_batch_full_size_one_step_sampled():
         op = O.Operator(w, K=16, s=s, bb_mode=0, targets=t).check()
         fo = O.bgk_step(op, f0, bench.tau_of(re, s))
         assert np.abs(fg[first:first + count][t] - fo).max() < pop_tol(1), (re, s)
+
+
+def test_porous_batch_full_size_sampled_and_graph_replay():
+    """The benchmark's launch configuration: the 64 porous samples (seeds
+    1000..1063, 13.3M nodes, tau = 1, interpolated bounce-back) in one
+    batched context at full size with the autotuned variant.  One step from
+    a random state: 30 sampled nodes of every sample (plus link nodes)
+    checked one by one against the oracle.  Then 16 steps replayed from the
+    captured graph equal 16 direct launches bit for bit at this size."""
+    specs = I.porous_batch_specs(64)
+    ws = I.generate(specs, procs=16)
+    sts = [mlbm.build_stencils_for(w, K=16, s=sp["s"], bb_mode=1) for w, sp in zip(ws, specs)]
+    ps = [mlbm.Params(mlbm.MODEL_TAU1, 1.0, 0.0, sp["g"], 0.0) for sp in specs]
+    ctx = mlbm.batch_init(sts, ps)
+    v, _ = mlbm.autotune(ctx, 3)
+    n = sum(w.n for w in ws)
+    rng = np.random.default_rng(8)
+    ru = np.stack([1 + (0.01 * rng.standard_normal(n)).astype(np.float32).astype(np.float64),
+                   (0.01 * rng.standard_normal(n)).astype(np.float32).astype(np.float64),
+                   (0.01 * rng.standard_normal(n)).astype(np.float32).astype(np.float64)], 1)
+    mlbm.set_fields(ctx, ru)
+    mlbm.step(ctx, 1)
+    b = mlbm.get_fields(ctx)
+    for i, (w, sp) in enumerate(zip(ws, specs)):
+        first, count = mlbm.batch_range(ctx, i)
+        ex = mlbm.stencils_export(sts[i])
+        t = _sample_targets(w, 30, 300 + i, np.nonzero(ex["link_mask"])[0])
+        op = O.Operator(w, K=16, s=sp["s"], bb_mode=1, targets=t).check()
+        a = O.mlbm1_step(op, ru[first:first + count], (sp["g"], 0.0))
+        assert np.abs(b[first:first + count][t] - a).max() < 5 * pop_tol(1), (i, v)
+    # graph replay (as the bench's timed steps) against direct launches
+    direct = mlbm.batch_init(sts, ps)
+    mlbm.set_kernel_variant(direct, v)
+    mlbm.set_graphs(direct, False)
+    for c in (ctx, direct):
+        mlbm.set_fields(c, ru)
+    mlbm.prepare_graphs(ctx)
+    mlbm.step(ctx, 16)
+    mlbm.step(direct, 16)
+    assert np.array_equal(mlbm.get_fields(ctx), mlbm.get_fields(direct))
