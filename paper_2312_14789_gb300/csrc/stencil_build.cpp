@@ -411,7 +411,73 @@ bool find_block(const double* off, int K, const double* dx, const double* dy, co
 
 // Bounce-back links of node (x, y).  Returns 0, or 8 when the node is inside
 // a solid.
-int links_of(double x, double y, double s, const Box& b, const double* disks, int nd, uint16_t* mask, double* q) {
+// Disks binned by the cells of a uniform grid over the box that their circle
+// (and each periodic image's), grown by `reach`, overlaps.  A departure
+// segment from a node is at most sqrt(2) s long, so with reach > sqrt(2) s a
+// disk that can meet it, or contains or touches the node, is listed in the
+// node's cell: testing those disks gives the result of testing all of them.
+struct DiskGrid {
+    double x0 = 0, y0 = 0, x1 = 0, y1 = 0, c = 1;
+    int ncx = 0, ncy = 0;
+    std::vector<int> start, items;
+    // the disks to test for a node at (x, y): ids[0..*n), or all disks when
+    // the node lies outside the grid (ids = nullptr)
+    const int* at(double x, double y, int* n) const {
+        if (ncx == 0 || !(x >= x0 && x <= x1 && y >= y0 && y <= y1)) return nullptr;
+        const int i = std::min(ncx - 1, (int)std::floor((x - x0) / c));
+        const int j = std::min(ncy - 1, (int)std::floor((y - y0) / c));
+        const int k = j * ncx + i;
+        *n = start[k + 1] - start[k];
+        return items.data() + start[k];
+    }
+};
+
+DiskGrid make_disk_grid(const Box& b, const double* disks, int nd, double reach) {
+    DiskGrid g;
+    if (nd == 0) return g;
+    double rmax = 0;
+    for (int d = 0; d < nd; ++d) rmax = std::max(rmax, disks[3 * d + 2]);
+    g.x0 = b.x0;
+    g.y0 = b.y0;
+    g.x1 = b.x1;
+    g.y1 = b.y1;
+    g.c = std::max({2.0 * reach, 0.5 * rmax, std::max(b.lx, b.ly) / 2048.0});
+    g.ncx = std::max(1, (int)std::ceil(b.lx / g.c));
+    g.ncy = std::max(1, (int)std::ceil(b.ly / g.c));
+    std::vector<std::vector<int>> cells((size_t)g.ncx * g.ncy);
+    for (int d = 0; d < nd; ++d)
+        for (int ix = -1; ix <= 1; ++ix) {
+            if (ix != 0 && !b.px) continue;
+            for (int iy = -1; iy <= 1; ++iy) {
+                if (iy != 0 && !b.py) continue;
+                const double cx = disks[3 * d] + ix * b.lx, cy = disks[3 * d + 1] + iy * b.ly;
+                const double r = disks[3 * d + 2] + reach;
+                const double lo_x = cx - r, hi_x = cx + r, lo_y = cy - r, hi_y = cy + r;
+                if (hi_x < g.x0 || lo_x > g.x1 || hi_y < g.y0 || lo_y > g.y1) continue;
+                const int i0 = std::max(0, (int)std::floor((lo_x - g.x0) / g.c));
+                const int i1 = std::min(g.ncx - 1, (int)std::floor((hi_x - g.x0) / g.c));
+                const int j0 = std::max(0, (int)std::floor((lo_y - g.y0) / g.c));
+                const int j1 = std::min(g.ncy - 1, (int)std::floor((hi_y - g.y0) / g.c));
+                for (int j = j0; j <= j1; ++j)
+                    for (int i = i0; i <= i1; ++i) cells[(size_t)j * g.ncx + i].push_back(d);
+            }
+        }
+    g.start.assign(cells.size() + 1, 0);
+    for (size_t k = 0; k < cells.size(); ++k) {
+        std::sort(cells[k].begin(), cells[k].end());
+        cells[k].erase(std::unique(cells[k].begin(), cells[k].end()), cells[k].end());
+        g.start[k + 1] = g.start[k] + (int)cells[k].size();
+    }
+    g.items.reserve((size_t)g.start.back());
+    for (const auto& v : cells) g.items.insert(g.items.end(), v.begin(), v.end());
+    return g;
+}
+
+// Bounce-back links of a node: for each direction, the fraction q of the
+// departure segment at which it first meets a solid side or disk (every
+// periodic image of the disks `ids` lists; all nd disks when ids is NULL).
+int links_of(double x, double y, double s, const Box& b, const double* disks, const int* ids, int nd,
+             uint16_t* mask, double* q) {
     const double tol = 1e-9 * s;
     *mask = 0;
     for (int k = 0; k < 9; ++k) q[k] = 0;
@@ -430,7 +496,8 @@ int links_of(double x, double y, double s, const Box& b, const double* disks, in
         if (b.side[3] == MLBM_SIDE_SOLID && vy > 0 && side_hit(b.y1 - y, vy)) return 8;
         if (b.side[0] == MLBM_SIDE_SOLID && vx < 0 && side_hit(x - b.x0, -vx)) return 8;
         if (b.side[1] == MLBM_SIDE_SOLID && vx > 0 && side_hit(b.x1 - x, vx)) return 8;
-        for (int d = 0; d < nd; ++d) {
+        for (int m = 0; m < nd; ++m) {
+            const int d = ids ? ids[m] : m;
             for (int ix = -1; ix <= 1; ++ix) {
                 if (ix != 0 && !b.px) continue;
                 for (int iy = -1; iy <= 1; ++iy) {
@@ -595,6 +662,7 @@ mlbm_status build_impl(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K,
     H.box_area = b.lx * b.ly;
     const double* xy = nodes->xy;
     const CellGrid grid = make_grid(xy, n, b, K);
+    const DiskGrid disk_grid = make_disk_grid(b, geo->disks, geo->n_disks, 1.5 * s);
 
     // caller-order work arrays (nid, Mc, Wc in the device stencil width Kw)
     std::vector<int64_t> nid((size_t)n * Kw);
@@ -623,7 +691,10 @@ mlbm_status build_impl(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K,
                 kind[i] = kKindEq;
                 continue;
             }
-            int code = links_of(xy[2 * i], xy[2 * i + 1], s, b, geo->disks, geo->n_disks, &mask[i], &qc[(size_t)i * 9]);
+            int n_ids = geo->n_disks;
+            const int* ids = disk_grid.at(xy[2 * i], xy[2 * i + 1], &n_ids);
+            if (!ids) n_ids = geo->n_disks;
+            int code = links_of(xy[2 * i], xy[2 * i + 1], s, b, geo->disks, ids, n_ids, &mask[i], &qc[(size_t)i * 9]);
             if (code) {
 #pragma omp critical
                 { if (bad_node < 0 || i < bad_node) { bad_node = i; bad_code = code; } }
