@@ -793,6 +793,8 @@ mlbm_status build_impl(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K,
     I.n = n;
     I.K = Kw;
     I.s = s;
+    int64_t n_wls = 0, n_lag = 0, n_eq = 0, n_link_nodes = 0, n_links = 0;
+#pragma omp parallel for schedule(static, 4096) reduction(+ : n_wls, n_lag, n_eq, n_link_nodes, n_links)
     for (int64_t p = 0; p < n; ++p) {
         const int64_t i = H.perm[p];
         for (int j = 0; j < Kw; ++j) H.idx[(size_t)p * Kw + j] = (int32_t)H.inv[nid[(size_t)i * Kw + j]];
@@ -807,14 +809,19 @@ mlbm_status build_impl(const mlbm_nodes* nodes, const mlbm_geometry* geo, int K,
         if (kind[i] == kKindEq)
             for (int c = 0; c < 3; ++c) H.eqv[(size_t)p * 3 + c] = nodes->eq_values[(size_t)i * 3 + c];
         H.area[p] = nodes->area ? nodes->area[i] : 1.0;
-        if (kind[i] == kKindWls) I.n_wls++;
-        else if (kind[i] == kKindLagrange) I.n_lagrange++;
-        else I.n_eq++;
+        if (kind[i] == kKindWls) n_wls++;
+        else if (kind[i] == kKindLagrange) n_lag++;
+        else n_eq++;
         if (mask[i]) {
-            I.n_link_nodes++;
-            for (int k = 1; k < 9; ++k) I.n_links += (mask[i] >> k) & 1;
+            n_link_nodes++;
+            for (int k = 1; k < 9; ++k) n_links += (mask[i] >> k) & 1;
         }
     }
+    I.n_wls = n_wls;
+    I.n_lagrange = n_lag;
+    I.n_eq = n_eq;
+    I.n_link_nodes = n_link_nodes;
+    I.n_links = n_links;
     I.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = st;
     return MLBM_OK;
